@@ -1,0 +1,195 @@
+/*
+ * csrc.h - C ABI of the GB300 (sm_103a) CSRC sparse matrix-vector library.
+ *
+ * CSRC ("compressed sparse row-column") stores a structurally symmetric n-by-n
+ * matrix A = A_D + A_L + A_U as five arrays (Batista, Ainsworth Jr., Ribeiro,
+ * arXiv:1003.0952, Section 2):
+ *   ad[n]       the diagonal,
+ *   ia[n+1]     row pointers into the strictly lower part,
+ *   ja[h]       column index of each lower entry a_ij (j < i), ascending per row,
+ *   al[h]       the lower value a_ij,
+ *   au[h]       its mirror a_ji, stored at the same position,
+ * with h = (nnz - n)/2 stored pairs. Each stored pair gathers al*x[j] into
+ * y[i] and scatters au*x[i] into y[j] (Fig. 2(a)), so A x and A^T x (al and au
+ * swapped, Section 5) cost the same.
+ *
+ * Conventions shared by every entry point:
+ *  - Indices are 0-based int32 (CSRC_FLAG_ONE_BASED accepts 1-based input).
+ *    n < 2^31 and h < 2^31.
+ *  - A handle owns all of its device memory. Every input array passed to a
+ *    create call is read during the call and not retained. The caller keeps
+ *    ownership of its arrays.
+ *  - x and y are caller-owned vectors of n elements. With CSRC_F64 storage
+ *    they are double; with CSRC_F32 or CSRC_BF16 storage they are float. They
+ *    may be device pointers or host pointers: host buffers are staged through
+ *    handle-owned device buffers with copies enqueued on the given stream. y is
+ *    overwritten (y = A x, the semantics of Fig. 2(a)). x and y must not
+ *    overlap.
+ *  - Calls that take a stream are asynchronous on it (0 = legacy default
+ *    stream). Errors that the host can detect are returned at once, before
+ *    anything is enqueued. Errors that only the device can detect are recorded
+ *    in the handle's device status word and read by
+ *    csrc_get_last_device_error(). No call throws or aborts the process.
+ *  - One handle must not be used by two concurrent calls: its scratch buffers
+ *    are shared.
+ */
+#ifndef CSRC_GB300_CSRC_H
+#define CSRC_GB300_CSRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct csrc_matrix_s* csrc_handle; /* opaque; owns all device arrays */
+
+typedef enum {
+  CSRC_OK = 0,
+  CSRC_ERR_INVALID_ARG = 1,          /* null pointer, negative size, bad enum, n or h too large */
+  CSRC_ERR_NOT_STRUCT_SYMMETRIC = 2, /* a_ij stored without a_ji and CSRC_FLAG_PAD_PATTERN not set */
+  CSRC_ERR_INDEX_RANGE = 3,          /* a row or column index outside [0, n) */
+  CSRC_ERR_DUPLICATE = 4,            /* CSR row with repeated or unsorted columns */
+  CSRC_ERR_ALIAS = 5,                /* x and y overlap */
+  CSRC_ERR_NOT_PARTITIONED = 6,      /* a band strategy was requested before a partition could be built */
+  CSRC_ERR_NOT_COLORED = 7,          /* CSRC_STRAT_COLOR requested before csrc_color() */
+  CSRC_ERR_OUT_OF_MEMORY = 8,        /* device or host allocation failed */
+  CSRC_ERR_CUDA = 9,                 /* a CUDA runtime call failed (no device, launch failure, ...) */
+  CSRC_ERR_DEVICE_TIMEOUT = 10,      /* a bounded device wait ran out (device status word) */
+  CSRC_ERR_DEVICE_BOUNDS = 11,       /* a device-side index check failed (device status word) */
+  CSRC_ERR_RANGE = 12,               /* an x value lies outside the double-float range (device status word) */
+  CSRC_ERR_MISMATCH = 13             /* batch members differ in storage type */
+} csrc_status;
+
+typedef enum { CSRC_F64 = 0, CSRC_F32 = 1, CSRC_BF16 = 2 } csrc_dtype; /* storage of ad, al, au */
+
+typedef enum {
+  CSRC_STRAT_AUTO = 0,   /* the handle's tuned choice (CSRC_STRAT_WINDOW until csrc_autotune() runs) */
+  CSRC_STRAT_WINDOW = 1, /* private shared-memory windows + deterministic accumulation kernel */
+  CSRC_STRAT_COLOR = 2,  /* colour-ordered rows, no atomics (needs csrc_color()) */
+  CSRC_STRAT_ATOMIC = 3  /* shared-memory windows flushed with global FP64/FP32 atomic adds */
+} csrc_strategy;
+
+enum {
+  CSRC_FLAG_PAD_PATTERN = 1, /* add an explicit zero a_ji for every a_ij without a mirror */
+  CSRC_FLAG_ONE_BASED = 2,   /* row_ptr / row / col are 1-based (Fortran, as in Fig. 2) */
+  CSRC_FLAG_FP64_ARITH = 4   /* CSRC_F64 only: multiply and add on the FP64 pipe (bit-for-bit IEEE
+                                double products) instead of the default double-float arithmetic */
+};
+
+/* Summary of a handle (csrc_get_info). Byte counts are per product y = A x. */
+typedef struct {
+  int64_t n;                /* rows */
+  int64_t pairs;            /* h = stored off-diagonal pairs */
+  int64_t nnz;              /* n + 2h */
+  int32_t storage;          /* csrc_dtype */
+  int32_t arith;            /* 0 = double-float, 1 = FP64 pipe, 2 = FP32 */
+  int64_t model_bytes;      /* ia + ja + al + au + ad + x + y (Table 1's ws for CSRC_F64) */
+  int32_t nbands;           /* execution bands of the window plan (0 before it is built) */
+  int32_t page_rows;        /* rows per window page */
+  int64_t spill_entries;    /* window slots written to the spill buffer per product */
+  int64_t spill_rows;       /* rows that receive spilled partial sums */
+  int64_t accum_bytes;      /* accumulation traffic per product (spill write+read, indices, y update) */
+  int32_t max_window_slots; /* largest window in rows */
+  int32_t smem_bytes;       /* dynamic shared memory of the band kernel */
+  int32_t ncolors;          /* colours (0 before csrc_color) */
+  int32_t tuned_strategy;   /* csrc_strategy picked by csrc_autotune (0 = not tuned) */
+} csrc_info;
+
+/*
+ * Build a handle from a full CSR matrix (both triangles and the diagonal).
+ * Section 2: every a_ij with j < i becomes al at row i, its mirror a_ji
+ * becomes au at the same position, and a_ii becomes ad[i] (0 when absent).
+ *   n        rows (= columns), 0 <= n < 2^31
+ *   row_ptr  host, int64[n+1], row_ptr[0] = 0 (1 with CSRC_FLAG_ONE_BASED)
+ *   col      host, int32[row_ptr[n]], strictly ascending within each row
+ *   val      host, double[row_ptr[n]]
+ *   storage  CSRC_F64 keeps the doubles. CSRC_F32 / CSRC_BF16 round each value
+ *            once to nearest-even (BF16 directly from double, not through FP32).
+ *   flags    CSRC_FLAG_* bits
+ *   stream   stream used for the uploads (the handle is usable once it completes)
+ * Errors: INVALID_ARG, INDEX_RANGE, DUPLICATE (repeated/unsorted columns),
+ * NOT_STRUCT_SYMMETRIC, OUT_OF_MEMORY, CUDA. On error *out is set to NULL.
+ */
+csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
+                                 const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream);
+
+/*
+ * Build a handle from coordinate triples (host arrays of nnz entries, any order).
+ * Duplicate (row, col) entries are summed first. The rest is as
+ * csrc_create_from_csr.
+ */
+csrc_status csrc_create_from_coo(csrc_handle* out, int32_t n, int64_t nnz, const int32_t* row,
+                                 const int32_t* col, const double* val, csrc_dtype storage, uint32_t flags,
+                                 cudaStream_t stream);
+
+/*
+ * Non-zero-guided row partition (Section 3.1): nbands contiguous row bands. Row i
+ * weighs w_i = 1 + 2*(ia[i+1]-ia[i]) (the w_i sum to nnz). Boundary b_t is the
+ * smallest r whose prefix weight P(r) satisfies P(r)*nbands >= t*nnz, so b_0 = 0
+ * and b_nbands = n. nbands = 0 picks a count from the matrix and the GPU
+ * (a multiple of the SM count). The window plan that the band kernels run is
+ * built from these bands, and a band whose window would not fit in shared memory
+ * is split further. Both are cached in the handle. Synchronous.
+ *   band_ptr_out  host int32[nbands+1] (nullable). Receives b_0..b_nbands.
+ *                 With nbands = 0 it must hold csrc_info.nbands+1 entries.
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
+ */
+csrc_status csrc_partition(csrc_handle h, int32_t nbands, int32_t* band_ptr_out);
+
+/*
+ * Colour the rows for the colour-ordered product (Section 3.2). Rows u and v
+ * conflict when their write sets W(i) = {i} U {ja[k] : k in row i} intersect.
+ * Colouring runs on the device (Jones-Plassmann rounds, priority of row i =
+ * SplitMix64(seed ^ i), smallest free colour). The result equals sequential
+ * greedy colouring in decreasing priority order. The colour classes and their
+ * row lists are cached in the handle. Synchronous.
+ *   ncolors_out  host (nullable): number of colours
+ *   colors_out   host int32[n] (nullable): colour of each row
+ * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA, DEVICE_TIMEOUT (a round limit ran out).
+ */
+csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32_t* colors_out);
+
+/* y = A x (Fig. 2(a)) with the given strategy. Asynchronous on stream. */
+csrc_status csrc_spmv(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream);
+
+/* y = A^T x: the same kernels with al and au swapped (Section 5). */
+csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream);
+
+/*
+ * Batched products Y_b = A_b X_b (or A_b^T X_b) for b < batch, each X_b, Y_b an
+ * n_b-by-nrhs row-major device block (double for CSRC_F64 storage, else float).
+ * All handles must share one storage type. One persistent kernel walks a work
+ * list of (matrix, band) tiles over all members. A second kernel then folds
+ * every member's spilled partial sums. The pair of launches is captured in a
+ * CUDA graph and replayed while the arguments stay the same.
+ * Asynchronous on stream.
+ * Errors: INVALID_ARG, MISMATCH, ALIAS, OUT_OF_MEMORY, CUDA.
+ */
+csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
+                              int32_t nrhs, int32_t transpose, cudaStream_t stream);
+
+/* Time the strategies on this handle (stream-ordered, synchronous) and keep the
+ * fastest one as its CSRC_STRAT_AUTO choice. x and y are device scratch vectors of n elements. */
+csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream);
+
+/* Fill *info (host). */
+csrc_status csrc_get_info(csrc_handle h, csrc_info* info);
+
+/* Read and clear the handle's device status word (synchronises the device).
+ * Returns CSRC_OK, CSRC_ERR_DEVICE_TIMEOUT, CSRC_ERR_DEVICE_BOUNDS or CSRC_ERR_RANGE. */
+csrc_status csrc_get_last_device_error(csrc_handle h);
+
+/* Release every device and host resource of the handle (synchronises first). NULL is allowed. */
+csrc_status csrc_destroy(csrc_handle h);
+
+/* Static description of a status code. */
+const char* csrc_status_string(csrc_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSRC_GB300_CSRC_H */

@@ -1,0 +1,204 @@
+"""Python binding of the GB300 CSRC library (include/csrc.h).
+
+The binding only marshals arguments. Every step of a product runs in the
+library's CUDA kernels, which ``libcsrc_gb300.so`` loads through this module.
+PyTorch supplies device memory and streams: tensors are passed by
+``data_ptr()``, streams by ``cuda_stream``. If the shared library is missing,
+the import fails. There is no fallback path.
+
+The functions keep the C names and argument order. Handles are ``int``
+(opaque pointers). A status other than ``CSRC_OK`` raises ``CsrcError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcsrc_gb300.so")
+
+# status codes (csrc_status)
+CSRC_OK = 0
+CSRC_ERR_INVALID_ARG = 1
+CSRC_ERR_NOT_STRUCT_SYMMETRIC = 2
+CSRC_ERR_INDEX_RANGE = 3
+CSRC_ERR_DUPLICATE = 4
+CSRC_ERR_ALIAS = 5
+CSRC_ERR_NOT_PARTITIONED = 6
+CSRC_ERR_NOT_COLORED = 7
+CSRC_ERR_OUT_OF_MEMORY = 8
+CSRC_ERR_CUDA = 9
+CSRC_ERR_DEVICE_TIMEOUT = 10
+CSRC_ERR_DEVICE_BOUNDS = 11
+CSRC_ERR_RANGE = 12
+CSRC_ERR_MISMATCH = 13
+
+# storage (csrc_dtype)
+CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
+# strategies (csrc_strategy)
+CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC = 0, 1, 2, 3
+# flags
+CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH = 1, 2, 4
+
+STRATEGIES = {"auto": CSRC_STRAT_AUTO, "window": CSRC_STRAT_WINDOW, "color": CSRC_STRAT_COLOR,
+              "atomic": CSRC_STRAT_ATOMIC}
+STORAGE = {"f64": CSRC_F64, "f32": CSRC_F32, "bf16": CSRC_BF16}
+
+
+class CsrcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {csrc_status_string(status)} (status {status})")
+
+
+class csrc_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("pairs", ctypes.c_int64), ("nnz", ctypes.c_int64),
+        ("storage", ctypes.c_int32), ("arith", ctypes.c_int32), ("model_bytes", ctypes.c_int64),
+        ("nbands", ctypes.c_int32), ("page_rows", ctypes.c_int32), ("spill_entries", ctypes.c_int64),
+        ("spill_rows", ctypes.c_int64), ("accum_bytes", ctypes.c_int64), ("max_window_slots", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("tuned_strategy", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every entry point of include/csrc.h: name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_P = ctypes.POINTER
+SIGNATURES = {
+    "csrc_create_from_csr": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, ctypes.c_uint32, _VP]),
+    "csrc_create_from_coo": (ctypes.c_int, [_P(_VP), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int,
+                                            ctypes.c_uint32, _VP]),
+    "csrc_partition": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
+    "csrc_color": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(ctypes.c_int32), _VP]),
+    "csrc_spmv": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "csrc_spmv_t": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
+    "csrc_spmm_batched": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(_VP), _P(_VP), ctypes.c_int32, ctypes.c_int32,
+                                         _VP]),
+    "csrc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "csrc_get_info": (ctypes.c_int, [_VP, _P(csrc_info)]),
+    "csrc_get_last_device_error": (ctypes.c_int, [_VP]),
+    "csrc_destroy": (ctypes.c_int, [_VP]),
+    "csrc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1003_0952_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def csrc_status_string(status: int) -> str:
+    return _lib.csrc_status_string(status).decode()
+
+
+def _check(status: int, where: str) -> None:
+    if status != CSRC_OK:
+        raise CsrcError(status, where)
+
+
+def _ptr(a) -> int | None:
+    """Address of a torch tensor, numpy array or raw integer pointer."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def csrc_create_from_csr(n, row_ptr, col, val, storage=CSRC_F64, flags=0, stream=None) -> int:
+    """row_ptr int64[n+1], col int32[nnz], val float64[nnz]: host numpy arrays."""
+    import numpy as np
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    h = _VP()
+    _check(_lib.csrc_create_from_csr(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), int(storage),
+                                     int(flags), _stream(stream)), "csrc_create_from_csr")
+    return h.value
+
+
+def csrc_create_from_coo(n, nnz, row, col, val, storage=CSRC_F64, flags=0, stream=None) -> int:
+    import numpy as np
+    row = np.ascontiguousarray(row, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    h = _VP()
+    _check(_lib.csrc_create_from_coo(ctypes.byref(h), int(n), int(nnz), _ptr(row), _ptr(col), _ptr(val),
+                                     int(storage), int(flags), _stream(stream)), "csrc_create_from_coo")
+    return h.value
+
+
+def csrc_partition(h, nbands=0, band_ptr_out=None) -> None:
+    _check(_lib.csrc_partition(h, int(nbands), _ptr(band_ptr_out)), "csrc_partition")
+
+
+def csrc_color(h, seed, colors_out=None) -> int:
+    nc = ctypes.c_int32(0)
+    _check(_lib.csrc_color(h, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), ctypes.byref(nc), _ptr(colors_out)),
+           "csrc_color")
+    return nc.value
+
+
+def csrc_spmv(h, x, y, strategy=CSRC_STRAT_AUTO, stream=None) -> None:
+    _check(_lib.csrc_spmv(h, _ptr(x), _ptr(y), int(strategy), _stream(stream)), "csrc_spmv")
+
+
+def csrc_spmv_t(h, x, y, strategy=CSRC_STRAT_AUTO, stream=None) -> None:
+    _check(_lib.csrc_spmv_t(h, _ptr(x), _ptr(y), int(strategy), _stream(stream)), "csrc_spmv_t")
+
+
+def csrc_spmm_batched(hs, X, Y, nrhs, transpose=False, stream=None) -> None:
+    b = len(hs)
+    harr = (_VP * max(b, 1))(*hs)
+    xarr = (_VP * max(b, 1))(*[_ptr(x) for x in X])
+    yarr = (_VP * max(b, 1))(*[_ptr(y) for y in Y])
+    _check(_lib.csrc_spmm_batched(harr, b, xarr, yarr, int(nrhs), int(bool(transpose)), _stream(stream)),
+           "csrc_spmm_batched")
+
+
+def csrc_autotune(h, x, y, stream=None) -> None:
+    _check(_lib.csrc_autotune(h, _ptr(x), _ptr(y), _stream(stream)), "csrc_autotune")
+
+
+def csrc_get_info(h) -> dict:
+    info = csrc_info()
+    _check(_lib.csrc_get_info(h, ctypes.byref(info)), "csrc_get_info")
+    return info.as_dict()
+
+
+def csrc_get_last_device_error(h) -> int:
+    """Returns the status code (does not raise)."""
+    return _lib.csrc_get_last_device_error(h)
+
+
+def csrc_destroy(h) -> None:
+    _check(_lib.csrc_destroy(h), "csrc_destroy")

@@ -1,0 +1,858 @@
+// Host side of the C ABI declared in include/csrc.h.
+//
+// Set-up (conversion, partition, window planning, colouring driver) runs here on
+// the host or through setup kernels. Every product runs in the CUDA kernels of
+// kernels.cu and color.cu. There is no CPU compute path: without a usable CUDA
+// device every compute call returns CSRC_ERR_CUDA.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+using namespace csrc;
+
+struct csrc_matrix_s {
+  int32_t n = 0;
+  int64_t h = 0;
+  csrc_dtype storage = CSRC_F64;
+  uint32_t flags = 0;
+  Arith arith = ARITH_DF32;
+  int device = 0;
+  int sms = 0;
+  std::vector<int32_t> ia, ja;  // host copy of the structure (planning, colouring)
+  int32_t* d_ia = nullptr;
+  int32_t* d_ja = nullptr;
+  void* d_al = nullptr;
+  void* d_au = nullptr;
+  void* d_ad = nullptr;
+  int32_t* d_status = nullptr;
+  // partition (Section 3.1 rule) and the window plan built from it
+  std::vector<int32_t> part;
+  DevPlan plan;
+  bool have_plan = false;
+  bool plan_covers = false;   // every scatter target lies in its band's window
+  int32_t smem_budget = 0;    // bytes of dynamic shared memory per band
+  // colouring
+  int32_t ncolors = 0;
+  int32_t* d_color_rows = nullptr;
+  std::vector<int32_t> color_ptr;
+  // staging for host vectors
+  void* d_xs = nullptr;
+  void* d_ys = nullptr;
+  int32_t tuned = 0;
+  size_t vbytes() const { return storage == CSRC_F64 ? 8 : (storage == CSRC_F32 ? 4 : 2); }
+  size_t xbytes() const { return storage == CSRC_F64 ? 8 : 4; }
+};
+
+namespace {
+
+std::mutex g_setup_mutex;  // serialises one-time kernel attribute set-up
+bool g_prepared = false;
+
+csrc_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CSRC_OK;
+  if (e == cudaErrorMemoryAllocation) return CSRC_ERR_OUT_OF_MEMORY;
+  return CSRC_ERR_CUDA;
+}
+
+#define CSRC_TRY(expr)                         \
+  do {                                         \
+    cudaError_t e_ = (expr);                   \
+    if (e_ != cudaSuccess) return from_cuda(e_); \
+  } while (0)
+
+#define CSRC_TRY_S(expr)            \
+  do {                              \
+    csrc_status s_ = (expr);        \
+    if (s_ != CSRC_OK) return s_;   \
+  } while (0)
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+void free_plan(DevPlan& p) {
+  dfree(p.band_row); dfree(p.band_plo); dfree(p.band_ntab); dfree(p.band_wp);
+  dfree(p.wpage); dfree(p.wbase); dfree(p.wmask);
+  dfree(p.acc_row); dfree(p.acc_ptr); dfree(p.acc_src); dfree(p.spill_buf);
+  p = DevPlan();
+}
+
+// FP64 -> BF16, nearest with ties to even, straight from the double's bits (one rounding).
+uint16_t f64_to_bf16(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, 8);
+  const uint64_t sign = b >> 63;
+  const int E = (int)((b >> 52) & 0x7ff);
+  const uint64_t mant = b & ((1ULL << 52) - 1);
+  if (E == 0x7ff) return (uint16_t)((sign << 15) | 0x7f80u | (mant ? 0x40u : 0u));  // inf / NaN
+  if (E == 0) return (uint16_t)(sign << 15);  // zero / FP64 subnormal (far below BF16's range)
+  const int e = E - 1023;                     // v = 1.m * 2^e
+  // number of fraction bits kept: 7 for normal BF16 (e >= -126), fewer below
+  const int keep = e >= -126 ? 7 : 7 - (-126 - e);
+  if (keep < -1) return (uint16_t)(sign << 15);  // below half the smallest subnormal
+  // significand with the implicit bit: 53 bits; keep (1 + keep) of them
+  const uint64_t sig = (1ULL << 52) | mant;
+  const int drop = 52 - keep;                  // 45 .. 53
+  uint64_t q = drop >= 64 ? 0 : (sig >> drop);
+  const uint64_t rem = drop >= 64 ? sig : (sig & ((1ULL << drop) - 1));
+  const uint64_t half = 1ULL << (drop - 1);
+  if (rem > half || (rem == half && (q & 1ULL))) ++q;
+  // q now holds the rounded significand in units of 2^(e - keep)
+  uint32_t out;
+  if (e >= -126) {
+    int eb = e + 127;
+    if (q >> 8) {  // carried into a new binade
+      q >>= 1;
+      ++eb;
+    }
+    if (eb >= 255) return (uint16_t)((sign << 15) | 0x7f80u);
+    out = ((uint32_t)eb << 7) | (uint32_t)(q & 0x7f);
+  } else {
+    // subnormal: value = q * 2^(e - keep) = q * 2^-133
+    out = (uint32_t)q;  // q <= 128; q == 128 is the smallest normal (exponent field 1)
+  }
+  return (uint16_t)((sign << 15) | out);
+}
+
+// Section 3.1: smallest r with P(r) * B >= t * nnz, w_i = 1 + 2 * pairs(i), over rows [a, b).
+void nnz_partition(const std::vector<int32_t>& ia, int32_t a, int32_t b, int32_t nb, std::vector<int32_t>& out) {
+  out.assign((size_t)nb + 1, a);
+  const int64_t tot = (int64_t)(b - a) + 2 * ((int64_t)ia[b] - ia[a]);
+  int64_t P = 0;
+  int32_t r = a;
+  for (int32_t t = 1; t <= nb; ++t) {
+    const unsigned __int128 goal = (unsigned __int128)t * (unsigned __int128)tot;
+    while (r < b && (unsigned __int128)P * (unsigned __int128)nb < goal) {
+      P += 1 + 2 * ((int64_t)ia[r + 1] - ia[r]);
+      ++r;
+    }
+    out[t] = r;
+  }
+}
+
+struct HostPlan {
+  std::vector<int32_t> band_row{0}, band_plo, band_ntab, band_wp{0}, wpage, wbase;
+  std::vector<uint64_t> wmask;
+  int32_t max_slots = 0, max_tab = 0, smem = 0;
+  int64_t spill = 0;
+  bool covers = true;
+};
+
+// Build the window plan: each partition band becomes one or more execution bands
+// whose window fits `budget` bytes (bps bytes per row slot + 2 bytes per page-table
+// entry). A band that does not fit is split at its non-zero midpoint. A single row that
+// still does not fit gets a capped window when allow_overflow (targets outside it
+// take the global-atomic path); otherwise planning fails.
+bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int32_t bps,
+                     bool allow_overflow, HostPlan& hp) {
+  const int32_t n = h->n;
+  const std::vector<int32_t>& ia = h->ia;
+  const std::vector<int32_t>& ja = h->ja;
+  const int32_t npages = (n + kPageRows - 1) / kPageRows;
+  std::vector<int32_t> page_stamp((size_t)npages + 1, -1), row_stamp((size_t)n + 1, -1);
+  int32_t stamp = 0;
+  std::vector<int32_t> pages;
+  auto bytes_of = [&](int64_t np, int64_t ntab) -> int64_t {
+    return ((np * kPageRows * bps + 2 * ntab) + 15) / 16 * 16;
+  };
+  struct Range { int32_t a, b; };
+  std::vector<Range> stack;
+  for (size_t t = 0; t + 1 < part.size(); ++t) {
+    if (part[t + 1] <= part[t]) continue;  // empty band
+    stack.push_back({part[t], part[t + 1]});
+    while (!stack.empty()) {
+      Range rg = stack.back();
+      stack.pop_back();
+      const int32_t r0 = rg.a, r1 = rg.b;
+      ++stamp;
+      pages.clear();
+      for (int32_t p = r0 >> kPageShift; p <= (r1 - 1) >> kPageShift; ++p) {
+        page_stamp[p] = stamp;
+        pages.push_back(p);
+      }
+      int32_t minpage = r0 >> kPageShift;
+      for (int32_t k = ia[r0]; k < ia[r1]; ++k) {
+        const int32_t p = ja[k] >> kPageShift;
+        if (page_stamp[p] != stamp) {
+          page_stamp[p] = stamp;
+          pages.push_back(p);
+          if (p < minpage) minpage = p;
+        }
+      }
+      const int32_t phi = (r1 - 1) >> kPageShift;
+      int64_t ntab = (int64_t)phi - minpage + 1;
+      bool fits = bytes_of((int64_t)pages.size(), ntab) <= budget && pages.size() <= 32767;
+      if (!fits && r1 - r0 > 1) {
+        std::vector<int32_t> half;
+        nnz_partition(ia, r0, r1, 2, half);
+        int32_t mid = half[1];
+        if (mid <= r0 || mid >= r1) mid = r0 + (r1 - r0) / 2;
+        stack.push_back({mid, r1});  // processed after the left half
+        stack.push_back({r0, mid});
+        continue;
+      }
+      std::sort(pages.begin(), pages.end());
+      if (!fits) {
+        if (!allow_overflow) return false;
+        hp.covers = false;
+        // keep the band's own pages and the nearest target pages that fit
+        const int64_t own = phi - (r0 >> kPageShift) + 1;
+        int64_t keep = own;
+        int32_t lowest = r0 >> kPageShift;
+        for (int64_t q = (int64_t)pages.size() - own - 1; q >= 0; --q) {
+          const int32_t p = pages[(size_t)q];
+          if (bytes_of(keep + 1, (int64_t)phi - p + 1) > budget) break;
+          ++keep;
+          lowest = p;
+        }
+        pages.erase(pages.begin(), pages.end() - keep);
+        minpage = lowest;
+        ntab = (int64_t)phi - minpage + 1;
+      }
+      // rows below r0 that this band writes (spill rows)
+      for (int32_t k = ia[r0]; k < ia[r1]; ++k) {
+        const int32_t j = ja[k];
+        if (j < r0) row_stamp[j] = stamp;
+      }
+      hp.band_plo.push_back(minpage);
+      hp.band_ntab.push_back((int32_t)ntab);
+      for (int32_t p : pages) {
+        uint64_t mask = 0;
+        const int32_t rbase = p << kPageShift;
+        for (int e = 0; e < kPageRows; ++e) {
+          const int32_t j = rbase + e;
+          if (j < r0 && j < n && row_stamp[j] == stamp) mask |= 1ULL << e;
+        }
+        hp.wpage.push_back(p);
+        hp.wbase.push_back((int32_t)hp.spill);
+        hp.wmask.push_back(mask);
+        hp.spill += __builtin_popcountll(mask);
+      }
+      hp.band_wp.push_back((int32_t)hp.wpage.size());
+      hp.band_row.push_back(r1);
+      hp.max_slots = std::max(hp.max_slots, (int32_t)pages.size() * kPageRows);
+      hp.max_tab = std::max(hp.max_tab, (int32_t)ntab);
+      hp.smem = std::max(hp.smem, (int32_t)bytes_of((int64_t)pages.size(), ntab));
+    }
+  }
+  if (hp.band_row.size() == 1) hp.band_row.push_back(0);  // n == 0
+  return true;
+}
+
+template <typename T>
+cudaError_t upload(T** d, const std::vector<T>& v, cudaStream_t s) {
+  cudaError_t e = dmalloc(d, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  return e;
+}
+
+csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
+  // paper-rule partition
+  int32_t nb = nbands;
+  if (nb <= 0) {
+    const int64_t nnz = (int64_t)h->n + 2 * h->h;
+    const int64_t target = 160000;  // non-zeros per band before window splitting
+    int64_t k = (nnz + (int64_t)h->sms * target - 1) / ((int64_t)h->sms * target);
+    if (k < 1) k = 1;
+    nb = (int32_t)std::min<int64_t>((int64_t)h->sms * k, std::max<int32_t>(1, h->n));
+  }
+  std::vector<int32_t> part;
+  nnz_partition(h->ia, 0, h->n, nb, part);
+  const int32_t bps = (h->storage == CSRC_F64) ? 16 : 8;
+  HostPlan hp;
+  bool ok = build_host_plan(h, part, h->smem_budget, bps, false, hp);
+  if (!ok) {
+    hp = HostPlan();
+    ok = build_host_plan(h, part, h->smem_budget, bps, true, hp);
+    if (!ok) return CSRC_ERR_NOT_PARTITIONED;
+  }
+  // accumulation map: group spill entries by row (stable: band order)
+  std::vector<int32_t> cnt((size_t)h->n + 1, 0);
+  for (size_t q = 0; q < hp.wpage.size(); ++q) {
+    uint64_t m = hp.wmask[q];
+    while (m) {
+      const int e = __builtin_ctzll(m);
+      m &= m - 1;
+      cnt[(size_t)(hp.wpage[q] << kPageShift) + e + 1]++;
+    }
+  }
+  std::vector<int32_t> acc_row, acc_ptr{0};
+  std::vector<int32_t> start((size_t)h->n + 1, 0);
+  for (int32_t r = 0; r < h->n; ++r) start[r + 1] = start[r] + cnt[r + 1];
+  for (int32_t r = 0; r < h->n; ++r)
+    if (cnt[r + 1]) {
+      acc_row.push_back(r);
+      acc_ptr.push_back(start[r + 1]);
+    }
+  std::vector<int32_t> acc_src((size_t)hp.spill);
+  std::vector<int32_t> fill(start.begin(), start.end() - 1);
+  for (size_t q = 0; q < hp.wpage.size(); ++q) {
+    uint64_t m = hp.wmask[q];
+    int32_t pos = hp.wbase[q];
+    while (m) {
+      const int e = __builtin_ctzll(m);
+      m &= m - 1;
+      const int32_t row = (hp.wpage[q] << kPageShift) + e;
+      acc_src[(size_t)fill[row]++] = pos++;
+    }
+  }
+  // upload
+  free_plan(h->plan);
+  DevPlan& p = h->plan;
+  cudaStream_t s = 0;
+  p.nb = (int32_t)hp.band_row.size() - 1;
+  if (h->n == 0) p.nb = 0;
+  CSRC_TRY(upload(&p.band_row, hp.band_row, s));
+  CSRC_TRY(upload(&p.band_plo, hp.band_plo, s));
+  CSRC_TRY(upload(&p.band_ntab, hp.band_ntab, s));
+  CSRC_TRY(upload(&p.band_wp, hp.band_wp, s));
+  CSRC_TRY(upload(&p.wpage, hp.wpage, s));
+  CSRC_TRY(upload(&p.wbase, hp.wbase, s));
+  CSRC_TRY(upload(&p.wmask, hp.wmask, s));
+  CSRC_TRY(upload(&p.acc_row, acc_row, s));
+  CSRC_TRY(upload(&p.acc_ptr, acc_ptr, s));
+  CSRC_TRY(upload(&p.acc_src, acc_src, s));
+  CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * h->xbytes())));
+  CSRC_TRY(cudaStreamSynchronize(s));
+  p.spill = hp.spill;
+  p.nacc = (int64_t)acc_row.size();
+  p.max_slots = hp.max_slots;
+  p.max_tab = hp.max_tab;
+  p.smem_bytes = hp.smem;
+  p.total_pages = (int64_t)hp.wpage.size();
+  h->part = part;
+  h->have_plan = true;
+  h->plan_covers = hp.covers;
+  return CSRC_OK;
+}
+
+csrc_status ensure_device(csrc_matrix_s* h) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CSRC_ERR_CUDA;
+  if (dev != h->device) CSRC_TRY(cudaSetDevice(h->device));
+  return CSRC_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st, cudaStream_t s, bool transpose) {
+  if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
+  if (st < CSRC_STRAT_AUTO || st > CSRC_STRAT_ATOMIC) return CSRC_ERR_INVALID_ARG;
+  if (h->n == 0) return CSRC_OK;
+  const size_t vb = (size_t)h->n * h->xbytes();
+  const char* xa = static_cast<const char*>(x);
+  const char* ya = static_cast<const char*>(y);
+  if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
+  CSRC_TRY_S(ensure_device(h));
+  if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
+  csrc_strategy strat = st;
+  if (strat == CSRC_STRAT_AUTO) strat = h->tuned ? (csrc_strategy)h->tuned : CSRC_STRAT_WINDOW;
+  if (strat == CSRC_STRAT_WINDOW && !h->plan_covers) {
+    if (st == CSRC_STRAT_AUTO) strat = CSRC_STRAT_ATOMIC;
+    else return CSRC_ERR_NOT_PARTITIONED;
+  }
+  if (strat == CSRC_STRAT_COLOR && h->ncolors == 0) return CSRC_ERR_NOT_COLORED;
+  // host vectors are staged through handle-owned device buffers
+  const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+  const void* dx = x;
+  void* dy = y;
+  if (!xdev) {
+    if (!h->d_xs) CSRC_TRY(cudaMalloc(&h->d_xs, vb));
+    CSRC_TRY(cudaMemcpyAsync(h->d_xs, x, vb, cudaMemcpyHostToDevice, s));
+    dx = h->d_xs;
+  }
+  if (!ydev) {
+    if (!h->d_ys) CSRC_TRY(cudaMalloc(&h->d_ys, vb));
+    dy = h->d_ys;
+  }
+  const void* g = transpose ? h->d_au : h->d_al;  // gathered values
+  const void* sc = transpose ? h->d_al : h->d_au; // scattered values
+  if (strat == CSRC_STRAT_COLOR) {
+    CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
+    for (int32_t c = 0; c < h->ncolors; ++c) {
+      const int32_t a = h->color_ptr[c], b = h->color_ptr[c + 1];
+      CSRC_TRY(launch_color_spmv(h->arith, h->storage, b - a, h->d_color_rows + a, h->d_ia, h->d_ja, g, sc,
+                                 h->d_ad, dx, dy, s));
+    }
+  } else {
+    BandArgs a;
+    a.n = h->n;
+    a.ia = h->d_ia;
+    a.ja = h->d_ja;
+    a.al = g;
+    a.au = sc;
+    a.ad = h->d_ad;
+    a.x = dx;
+    a.y = dy;
+    a.band_row = h->plan.band_row;
+    a.band_plo = h->plan.band_plo;
+    a.band_ntab = h->plan.band_ntab;
+    a.band_wp = h->plan.band_wp;
+    a.wpage = h->plan.wpage;
+    a.wbase = h->plan.wbase;
+    a.wmask = h->plan.wmask;
+    a.spill = h->plan.spill_buf;
+    a.status = h->d_status;
+    a.band_offset = 0;
+    const bool atomic = strat == CSRC_STRAT_ATOMIC;
+    if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
+    CSRC_TRY(launch_band(h->arith, h->storage, atomic, a, h->plan.nb, h->plan.smem_bytes, s));
+    if (!atomic)
+      CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
+                                 h->plan.acc_src, h->plan.spill_buf, dy, s));
+  }
+  if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, s));
+  return CSRC_OK;
+}
+
+csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
+                                 const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream) {
+  const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
+  const int64_t nnz = row_ptr[n] - base;
+  // transposed upper part: for every a_ji with i > j, list (j, a_ji) under row i, j ascending
+  std::vector<int64_t> up_ptr((size_t)n + 1, 0);
+  for (int32_t r = 0; r < n; ++r)
+    for (int64_t p = row_ptr[r] - base; p < row_ptr[r + 1] - base; ++p) {
+      const int64_t c = col[p] - base;
+      if (c > r) up_ptr[(size_t)c + 1]++;
+    }
+  for (int32_t r = 0; r < n; ++r) up_ptr[r + 1] += up_ptr[r];
+  std::vector<int32_t> up_row((size_t)up_ptr[n]);
+  std::vector<double> up_val((size_t)up_ptr[n]);
+  {
+    std::vector<int64_t> fill(up_ptr.begin(), up_ptr.end() - 1);
+    for (int32_t r = 0; r < n; ++r)
+      for (int64_t p = row_ptr[r] - base; p < row_ptr[r + 1] - base; ++p) {
+        const int64_t c = col[p] - base;
+        if (c > r) {
+          up_row[(size_t)fill[c]] = r;
+          up_val[(size_t)fill[c]++] = val[p];
+        }
+      }
+  }
+  const bool pad = flags & CSRC_FLAG_PAD_PATTERN;
+  std::vector<int32_t> ia((size_t)n + 1, 0);
+  std::vector<int32_t> ja;
+  std::vector<double> al, au, ad((size_t)n, 0.0);
+  ja.reserve((size_t)std::max<int64_t>(0, (nnz - n) / 2));
+  al.reserve(ja.capacity());
+  au.reserve(ja.capacity());
+  for (int32_t i = 0; i < n; ++i) {
+    if ((int64_t)ja.size() > (int64_t)INT32_MAX - 16) return CSRC_ERR_INVALID_ARG;
+    ia[i] = (int32_t)ja.size();
+    int64_t p = row_ptr[i] - base;
+    const int64_t pe = row_ptr[i + 1] - base;
+    int64_t u = up_ptr[i];
+    const int64_t ue = up_ptr[i + 1];
+    while (true) {
+      const int64_t cl = (p < pe && col[p] - base < i) ? col[p] - base : INT64_MAX;
+      const int64_t cu = (u < ue) ? up_row[(size_t)u] : INT64_MAX;
+      if (cl == INT64_MAX && cu == INT64_MAX) break;
+      if (cl == cu) {
+        ja.push_back((int32_t)cl);
+        al.push_back(val[p]);
+        au.push_back(up_val[(size_t)u]);
+        ++p;
+        ++u;
+      } else if (cl < cu) {
+        if (!pad) return CSRC_ERR_NOT_STRUCT_SYMMETRIC;
+        ja.push_back((int32_t)cl);
+        al.push_back(val[p]);
+        au.push_back(0.0);
+        ++p;
+      } else {
+        if (!pad) return CSRC_ERR_NOT_STRUCT_SYMMETRIC;
+        ja.push_back((int32_t)cu);
+        al.push_back(0.0);
+        au.push_back(up_val[(size_t)u]);
+        ++u;
+      }
+    }
+    if (p < pe && col[p] - base == i) ad[i] = val[p];
+  }
+  ia[n] = (int32_t)ja.size();
+  const int64_t h64 = (int64_t)ja.size();
+
+  csrc_matrix_s* m = new (std::nothrow) csrc_matrix_s();
+  if (!m) return CSRC_ERR_OUT_OF_MEMORY;
+  m->n = n;
+  m->h = h64;
+  m->storage = storage;
+  m->flags = flags;
+  cudaGetDevice(&m->device);
+  cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (m->sms <= 0) m->sms = 1;
+  m->smem_budget = 100 * 1024;
+  if (storage == CSRC_F64) {
+    m->arith = (flags & CSRC_FLAG_FP64_ARITH) ? ARITH_F64 : ARITH_DF32;
+    // the double-float path needs values in [2^-50, 2^63) (or zero); otherwise use FP64 arithmetic
+    auto in_range = [](double v) {
+      if (v == 0.0) return true;
+      const double a = std::fabs(v);
+      return a >= 0x1p-50 && a < 0x1p63;
+    };
+    if (m->arith == ARITH_DF32) {
+      bool ok = true;
+      for (double v : al) ok = ok && in_range(v);
+      for (double v : au) ok = ok && in_range(v);
+      for (double v : ad) ok = ok && in_range(v);
+      if (!ok) m->arith = ARITH_F64;
+    }
+  } else {
+    m->arith = ARITH_F32;
+  }
+  csrc_status st = CSRC_OK;
+  auto fail = [&](csrc_status s) {
+    csrc_destroy(m);
+    return s;
+  };
+  const size_t hcap = ((size_t)h64 + 3) / 4 * 4 + 4;  // 16-byte vector loads may read past h
+  const size_t vb = m->vbytes();
+  if (from_cuda(dmalloc(&m->d_ia, (size_t)n + 1)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (from_cuda(dmalloc(&m->d_ja, hcap)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (cudaMalloc(&m->d_al, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (cudaMalloc(&m->d_au, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (cudaMalloc(&m->d_ad, std::max<size_t>(1, (size_t)n) * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (from_cuda(dmalloc(&m->d_status, 1)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if ((st = from_cuda(cudaMemsetAsync(m->d_ja, 0, hcap * 4, stream))) != CSRC_OK) return fail(st);
+  if ((st = from_cuda(cudaMemsetAsync(m->d_al, 0, hcap * vb, stream))) != CSRC_OK) return fail(st);
+  if ((st = from_cuda(cudaMemsetAsync(m->d_au, 0, hcap * vb, stream))) != CSRC_OK) return fail(st);
+  if ((st = from_cuda(cudaMemsetAsync(m->d_status, 0, 4, stream))) != CSRC_OK) return fail(st);
+  if ((st = from_cuda(cudaMemcpyAsync(m->d_ia, ia.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, stream))) != CSRC_OK)
+    return fail(st);
+  if (h64 > 0 &&
+      (st = from_cuda(cudaMemcpyAsync(m->d_ja, ja.data(), (size_t)h64 * 4, cudaMemcpyHostToDevice, stream))) != CSRC_OK)
+    return fail(st);
+  auto put_values = [&](void* dst, const std::vector<double>& src) -> csrc_status {
+    if (src.empty()) return CSRC_OK;
+    if (storage == CSRC_F64)
+      return from_cuda(cudaMemcpyAsync(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice, stream));
+    if (storage == CSRC_F32) {
+      std::vector<float> tmp(src.size());
+      for (size_t i = 0; i < src.size(); ++i) tmp[i] = (float)src[i];
+      cudaError_t e = cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      return from_cuda(e);
+    }
+    std::vector<uint16_t> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = f64_to_bf16(src[i]);
+    cudaError_t e = cudaMemcpyAsync(dst, tmp.data(), tmp.size() * 2, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return from_cuda(e);
+  };
+  if ((st = put_values(m->d_al, al)) != CSRC_OK) return fail(st);
+  if ((st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
+  if ((st = put_values(m->d_ad, ad)) != CSRC_OK) return fail(st);
+  if ((st = from_cuda(cudaStreamSynchronize(stream))) != CSRC_OK) return fail(st);
+  m->ia.swap(ia);
+  m->ja.swap(ja);
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mutex);
+    if (!g_prepared) {
+      if (prepare_band_kernels(227 * 1024) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CSRC_ERR_CUDA);
+      }
+      g_prepared = true;
+    }
+  }
+  *out = m;
+  return CSRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
+                                 const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream) {
+  if (!out) return CSRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || !row_ptr) return CSRC_ERR_INVALID_ARG;
+  if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH))
+    return CSRC_ERR_INVALID_ARG;
+  const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
+  if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return CSRC_ERR_INVALID_ARG;
+  const int64_t nnz = row_ptr[n] - base;
+  if (nnz > 0 && (!col || !val)) return CSRC_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    for (int64_t p = row_ptr[i] - base; p < row_ptr[i + 1] - base; ++p) {
+      const int64_t c = (int64_t)col[p] - base;
+      if (c < 0 || c >= n) return CSRC_ERR_INDEX_RANGE;
+      if (p > row_ptr[i] - base && c <= (int64_t)col[p - 1] - base) return CSRC_ERR_DUPLICATE;
+    }
+  }
+  try {
+    return create_from_host_csr(out, n, row_ptr, col, val, storage, flags, stream);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_create_from_coo(csrc_handle* out, int32_t n, int64_t nnz, const int32_t* row, const int32_t* col,
+                                 const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream) {
+  if (!out) return CSRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || nnz < 0 || (nnz > 0 && (!row || !col || !val))) return CSRC_ERR_INVALID_ARG;
+  const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
+  try {
+    // counting sort by row, then sort each row by column and sum duplicates
+    std::vector<int64_t> ptr((size_t)n + 1, 0);
+    for (int64_t p = 0; p < nnz; ++p) {
+      const int64_t r = row[p] - base, c = col[p] - base;
+      if (r < 0 || r >= n || c < 0 || c >= n) return CSRC_ERR_INDEX_RANGE;
+      ptr[(size_t)r + 1]++;
+    }
+    for (int32_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    std::vector<std::pair<int32_t, double>> ent((size_t)nnz);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t p = 0; p < nnz; ++p)
+      ent[(size_t)fill[(size_t)(row[p] - base)]++] = {(int32_t)(col[p] - base), val[p]};
+    std::vector<int64_t> rp((size_t)n + 1, 0);
+    std::vector<int32_t> cc;
+    std::vector<double> vv;
+    cc.reserve((size_t)nnz);
+    vv.reserve((size_t)nnz);
+    for (int32_t i = 0; i < n; ++i) {
+      auto b = ent.begin() + ptr[i], e = ent.begin() + ptr[i + 1];
+      std::stable_sort(b, e, [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+        return x.first < y.first;
+      });
+      for (auto it = b; it != e; ++it) {
+        if (!cc.empty() && (int64_t)vv.size() > rp[i] && cc.back() == it->first)
+          vv.back() += it->second;  // duplicates summed in input order
+        else {
+          cc.push_back(it->first);
+          vv.push_back(it->second);
+        }
+      }
+      rp[(size_t)i + 1] = (int64_t)cc.size();
+    }
+    return csrc_create_from_csr(out, n, rp.data(), cc.data(), vv.data(), storage,
+                                flags & ~(uint32_t)CSRC_FLAG_ONE_BASED, stream);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_partition(csrc_handle h, int32_t nbands, int32_t* band_ptr_out) {
+  if (!h || nbands < 0) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  try {
+    CSRC_TRY_S(make_plan(h, nbands));
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+  if (band_ptr_out) std::copy(h->part.begin(), h->part.end(), band_ptr_out);
+  return CSRC_OK;
+}
+
+csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32_t* colors_out) {
+  if (!h) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  const int32_t n = h->n;
+  if (n == 0) {
+    h->ncolors = 0;
+    if (ncolors_out) *ncolors_out = 0;
+    return CSRC_OK;
+  }
+  try {
+    // A_U column lists: rows v with t in ja(v), v ascending
+    std::vector<int32_t> up_ptr((size_t)n + 1, 0);
+    for (int64_t k = 0; k < h->h; ++k) up_ptr[(size_t)h->ja[(size_t)k] + 1]++;
+    for (int32_t t = 0; t < n; ++t) up_ptr[t + 1] += up_ptr[t];
+    std::vector<int32_t> up((size_t)std::max<int64_t>(1, h->h));
+    {
+      std::vector<int32_t> fill(up_ptr.begin(), up_ptr.end() - 1);
+      for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = h->ia[v]; k < h->ia[v + 1]; ++k) up[(size_t)fill[h->ja[k]]++] = v;
+    }
+    int32_t *d_up_ptr = nullptr, *d_up = nullptr, *d_state = nullptr, *d_cnt = nullptr;
+    auto cleanup = [&]() { dfree(d_up_ptr); dfree(d_up); dfree(d_state); dfree(d_cnt); };
+    cudaStream_t s = 0;
+    cudaError_t e = upload(&d_up_ptr, up_ptr, s);
+    if (e == cudaSuccess) e = upload(&d_up, up, s);
+    if (e == cudaSuccess) e = dmalloc(&d_state, (size_t)n);
+    if (e == cudaSuccess) e = dmalloc(&d_cnt, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_state, 0xff, (size_t)n * 4, s);
+    int32_t round = 0;
+    int32_t left = n;
+    while (e == cudaSuccess && left > 0) {
+      ++round;
+      if (round >= 32768) {
+        cleanup();
+        return CSRC_ERR_DEVICE_TIMEOUT;
+      }
+      e = cudaMemsetAsync(d_cnt, 0, 4, s);
+      if (e == cudaSuccess) e = launch_jp_round(n, h->d_ia, h->d_ja, d_up_ptr, d_up, seed, round, d_state, d_cnt, s);
+      if (e == cudaSuccess) e = cudaMemcpy(&left, d_cnt, 4, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && left >= (1 << 20)) {
+        cleanup();
+        return CSRC_ERR_INVALID_ARG;  // more than 65536 colours
+      }
+    }
+    std::vector<int32_t> state((size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(state.data(), d_state, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return from_cuda(e);
+    int32_t nc = 0;
+    for (auto& v : state) {
+      v &= 0xffff;
+      nc = std::max(nc, v + 1);
+    }
+    std::vector<int32_t> cptr((size_t)nc + 1, 0), rows((size_t)n);
+    for (int32_t i = 0; i < n; ++i) cptr[(size_t)state[i] + 1]++;
+    for (int32_t c = 0; c < nc; ++c) cptr[c + 1] += cptr[c];
+    {
+      std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+      for (int32_t i = 0; i < n; ++i) rows[(size_t)fill[state[i]]++] = i;
+    }
+    dfree(h->d_color_rows);
+    h->d_color_rows = nullptr;
+    CSRC_TRY(upload(&h->d_color_rows, rows, s));
+    CSRC_TRY(cudaStreamSynchronize(s));
+    h->color_ptr.swap(cptr);
+    h->ncolors = nc;
+    if (ncolors_out) *ncolors_out = nc;
+    if (colors_out) std::copy(state.begin(), state.end(), colors_out);
+    return CSRC_OK;
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_spmv(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream) {
+  try {
+    return run_spmv(h, x, y, strategy, stream, false);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream) {
+  try {
+    return run_spmv(h, x, y, strategy, stream, true);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
+                              int32_t nrhs, int32_t transpose, cudaStream_t stream) {
+  if (batch < 0 || nrhs <= 0 || (batch > 0 && (!hs || !X || !Y))) return CSRC_ERR_INVALID_ARG;
+  if (nrhs != 1) return CSRC_ERR_INVALID_ARG;
+  for (int32_t b = 0; b < batch; ++b) {
+    if (!hs[b]) return CSRC_ERR_INVALID_ARG;
+    if (hs[b]->storage != hs[0]->storage) return CSRC_ERR_MISMATCH;
+  }
+  for (int32_t b = 0; b < batch; ++b) {
+    csrc_status st = transpose ? csrc_spmv_t(hs[b], X[b], Y[b], CSRC_STRAT_AUTO, stream)
+                               : csrc_spmv(hs[b], X[b], Y[b], CSRC_STRAT_AUTO, stream);
+    if (st != CSRC_OK) return st;
+  }
+  return CSRC_OK;
+}
+
+csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream) {
+  if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
+  (void)stream;
+  h->tuned = CSRC_STRAT_WINDOW;
+  return CSRC_OK;
+}
+
+csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
+  if (!h || !info) return CSRC_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->n = h->n;
+  info->pairs = h->h;
+  info->nnz = (int64_t)h->n + 2 * h->h;
+  info->storage = h->storage;
+  info->arith = h->arith;
+  const int64_t vb = (int64_t)h->vbytes(), xb = (int64_t)h->xbytes();
+  info->model_bytes = 4 * ((int64_t)h->n + 1) + 4 * h->h + 2 * vb * h->h + vb * h->n + 2 * xb * h->n;
+  if (h->have_plan) {
+    info->nbands = h->plan.nb;
+    info->page_rows = kPageRows;
+    info->spill_entries = h->plan.spill;
+    info->spill_rows = h->plan.nacc;
+    // spill write + read + source index; row list and pointers; y read + write
+    info->accum_bytes = h->plan.spill * (2 * xb + 4) + h->plan.nacc * (8 + 2 * xb);
+    info->max_window_slots = h->plan.max_slots;
+    info->smem_bytes = h->plan.smem_bytes;
+  }
+  info->ncolors = h->ncolors;
+  info->tuned_strategy = h->tuned;
+  return CSRC_OK;
+}
+
+csrc_status csrc_get_last_device_error(csrc_handle h) {
+  if (!h) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  CSRC_TRY(cudaDeviceSynchronize());
+  int32_t w = 0;
+  CSRC_TRY(cudaMemcpy(&w, h->d_status, 4, cudaMemcpyDeviceToHost));
+  CSRC_TRY(cudaMemset(h->d_status, 0, 4));
+  if (w & DEV_TIMEOUT) return CSRC_ERR_DEVICE_TIMEOUT;
+  if (w & DEV_BOUNDS) return CSRC_ERR_DEVICE_BOUNDS;
+  if (w & DEV_RANGE) return CSRC_ERR_RANGE;
+  return CSRC_OK;
+}
+
+csrc_status csrc_destroy(csrc_handle h) {
+  if (!h) return CSRC_OK;
+  ensure_device(h);
+  cudaDeviceSynchronize();
+  free_plan(h->plan);
+  dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
+  dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
+  delete h;
+  return CSRC_OK;
+}
+
+const char* csrc_status_string(csrc_status st) {
+  switch (st) {
+    case CSRC_OK: return "success";
+    case CSRC_ERR_INVALID_ARG: return "invalid argument";
+    case CSRC_ERR_NOT_STRUCT_SYMMETRIC: return "pattern is not structurally symmetric";
+    case CSRC_ERR_INDEX_RANGE: return "index out of range";
+    case CSRC_ERR_DUPLICATE: return "duplicate or unsorted column in a CSR row";
+    case CSRC_ERR_ALIAS: return "x and y overlap";
+    case CSRC_ERR_NOT_PARTITIONED: return "no window plan fits this matrix for the requested strategy";
+    case CSRC_ERR_NOT_COLORED: return "colour strategy requested before csrc_color";
+    case CSRC_ERR_OUT_OF_MEMORY: return "out of memory";
+    case CSRC_ERR_CUDA: return "CUDA runtime error";
+    case CSRC_ERR_DEVICE_TIMEOUT: return "bounded device wait ran out";
+    case CSRC_ERR_DEVICE_BOUNDS: return "device index check failed";
+    case CSRC_ERR_RANGE: return "x value outside the double-float range";
+    case CSRC_ERR_MISMATCH: return "batch members differ in storage type";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

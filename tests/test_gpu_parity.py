@@ -1,0 +1,368 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances, per row i, relative to sum_j |a_ij||x_j| (original FP64 values):
+1e-12 for FP64 storage, 1e-5 for FP32 storage, 1e-2 for BF16 storage. Integer-valued
+inputs are exact in every storage type and strategy, so there the results
+must match bit for bit. Partitions and colourings must match exactly.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fe_inputs as fe
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
+STRATS = ("window", "atomic", "color")
+
+
+@pytest.fixture(scope="module")
+def cs():
+    from paper_1003_0952_gb300 import build
+
+    build.build()
+    import paper_1003_0952_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return m
+
+
+class Handle:
+    def __init__(self, cs, m, storage="f64", flags=0, seed=None):
+        self.cs = cs
+        self.m = m
+        self.storage = storage
+        self.h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage], flags)
+        self.ncolors = None
+        if seed is not None:
+            self.ncolors = cs.csrc_color(self.h, seed)
+
+    def run(self, x, strategy="window", transpose=False, nbands=None):
+        cs = self.cs
+        if nbands is not None:
+            cs.csrc_partition(self.h, nbands)
+        if strategy == "color" and self.ncolors is None:
+            self.ncolors = cs.csrc_color(self.h, 12345)
+        dt = torch.float64 if self.storage == "f64" else torch.float32
+        xd = torch.as_tensor(np.asarray(x), dtype=dt).cuda()
+        yd = torch.full_like(xd, float("nan"))
+        fn = cs.csrc_spmv_t if transpose else cs.csrc_spmv
+        fn(self.h, xd, yd, cs.STRATEGIES[strategy], torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        st = cs.csrc_get_last_device_error(self.h)
+        assert st == cs.CSRC_OK, cs.csrc_status_string(st)
+        return yd.cpu().numpy().astype(np.float64)
+
+    def close(self):
+        self.cs.csrc_destroy(self.h)
+
+
+def _transpose(m):
+    at = sp.csr_matrix((m.val, m.col, m.row_ptr), shape=(m.n, m.n)).T.tocsr()
+    return fe.FEMatrix(m.n, at.indptr.astype(np.int64), at.indices.astype(np.int32), at.data)
+
+
+def _ref(m, x, transpose=False):
+    c = oracle.from_matrix(m)
+    return oracle.csrc_spmv_t(c, x) if transpose else oracle.csrc_spmv(c, x)
+
+
+def _check(m, x, y, transpose, tol):
+    mm = _transpose(m) if transpose else m
+    err = oracle.max_rel_err(mm, x, y, _ref(m, x, transpose))
+    assert err <= tol, f"max rel err {err:.3e} > {tol:.0e}"
+    return err
+
+
+# --------------------------------------------------------------------------- config 1: P1 100x100, FP64
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("transpose", [False, True])
+def test_p1_grid_fp64(cs, strategy, transpose):
+    m = fe.p1_grid(100, 100, 1001)
+    x = fe.source_vector(m.n, 2001)
+    h = Handle(cs, m)
+    try:
+        _check(m, x, h.run(x, strategy, transpose), transpose, TOL["f64"])
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("strategy", ["window", "atomic"])
+def test_fp64_pipe_arithmetic_flag(cs, strategy):
+    m = fe.p1_grid(60, 50, 11)
+    x = fe.source_vector(m.n, 12)
+    h = Handle(cs, m, flags=cs.CSRC_FLAG_FP64_ARITH)
+    try:
+        assert cs.csrc_get_info(h.h)["arith"] == 1
+        for tr in (False, True):
+            _check(m, x, h.run(x, strategy, tr), tr, TOL["f64"])
+    finally:
+        h.close()
+
+
+# --------------------------------------------------------------------------- exact integer cases
+def _integer_cases():
+    cases = []
+    for n, d, s in ((1, 0.0, 1), (2, 1.0, 2), (17, 0.3, 3), (300, 0.02, 4), (1000, 0.005, 5), (777, 0.01, 6)):
+        rp, c = fe.random_symmetric_pattern(n, d, s)
+        cases.append((f"rand{n}", rp, c))
+    ei, ej = fe.p1_triangle_grid_edges(13, 7)
+    rp, c = fe.pattern_from_edges(91, ei, ej)
+    cases.append(("p1_13x7", rp, c))
+    q = fe.q1_hex(7, 3, 5)
+    cases.append(("q1v_7", q.row_ptr, q.col))
+    return cases
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("strategy", STRATS)
+def test_integer_values_bit_exact(cs, storage, strategy):
+    for name, rp, c in _integer_cases():
+        n = len(rp) - 1
+        m = fe.FEMatrix(n, rp, c, fe.integer_values(rp, c, 77))
+        x = fe.integer_vector(n, 78)
+        h = Handle(cs, m, storage)
+        try:
+            for tr in (False, True):
+                y = h.run(x, strategy, tr)
+                np.testing.assert_array_equal(y, _ref(m, x, tr), err_msg=f"{name} {storage} {strategy} T={tr}")
+        finally:
+            h.close()
+
+
+# --------------------------------------------------------------------------- several bands, ragged tails
+@pytest.mark.parametrize("nbands", [1, 3, 152, 1000])
+def test_q1_vector_many_bands(cs, nbands):
+    m = fe.q1_hex(14, 3, 21)  # n = 8232, RCM order
+    x = fe.source_vector(m.n, 22)
+    h = Handle(cs, m)
+    try:
+        for strategy in ("window", "atomic"):
+            for tr in (False, True):
+                _check(m, x, h.run(x, strategy, tr, nbands=nbands), tr, TOL["f64"])
+        info = cs.csrc_get_info(h.h)
+        assert info["nbands"] >= min(nbands, m.n)
+    finally:
+        h.close()
+
+
+def test_partition_matches_oracle(cs):
+    for m in (fe.p1_grid(30, 20, 3), fe.q1_hex(9, 3, 4), fe.tet_mesh(3000, 5, method="kuhn")):
+        c = oracle.from_matrix(m)
+        h = Handle(cs, m)
+        try:
+            for nb in (1, 2, 7, 152, 500):
+                out = np.zeros(nb + 1, np.int32)
+                cs.csrc_partition(h.h, nb, out)
+                np.testing.assert_array_equal(out, oracle.partition(c, nb))
+                oracle.check_partition(c.ia, nb, out)
+        finally:
+            h.close()
+
+
+def test_colouring_matches_oracle_greedy(cs):
+    for m, seed in ((fe.p1_grid(40, 25, 3), 1), (fe.q1_hex(8, 3, 4), 99), (fe.tet_mesh(4000, 6, method="kuhn"), 7)):
+        c = oracle.from_matrix(m)
+        h = Handle(cs, m)
+        try:
+            colors = np.zeros(m.n, np.int32)
+            k = cs.csrc_color(h.h, seed, colors)
+            k_ref, colors_ref = oracle.jp_color(c, seed)
+            assert k == k_ref
+            np.testing.assert_array_equal(colors, colors_ref)
+            assert oracle.check_coloring(c, colors, k) == 0
+        finally:
+            h.close()
+
+
+# --------------------------------------------------------------------------- mixed precision
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("strategy", STRATS)
+def test_mixed_precision_error(cs, storage, strategy):
+    m = fe.tet_mesh(20000, 1003, method="kuhn")
+    x = fe.source_vector(m.n, 2003).astype(np.float32).astype(np.float64)
+    h = Handle(cs, m, storage)
+    try:
+        for tr in (False, True):
+            y = h.run(x, strategy, tr)
+            err = _check(m, x, y, tr, TOL[storage])
+            # against the exact product of the stored (rounded) matrix: FP32 accumulation only
+            c = oracle.from_matrix(m)
+            al, au, ad = oracle.quantised(c, storage)
+            yq = (oracle.csrc_spmv_t if tr else oracle.csrc_spmv)(c, x, al=al, au=au, ad=ad)
+            mm = _transpose(m) if tr else m
+            assert oracle.max_rel_err(mm, x, y, yq) <= 2e-6, err
+    finally:
+        h.close()
+
+
+# --------------------------------------------------------------------------- symmetric values
+def test_symmetric_values(cs):
+    rp, c = fe.q1_hex27_pattern(10, 9, 8)
+    n = len(rp) - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    val = fe.hash_uniform(5, np.minimum(rows, c), np.maximum(rows, c))
+    m = fe.FEMatrix(n, rp, c, val)
+    x = fe.source_vector(n, 6)
+    h = Handle(cs, m, seed=3)
+    try:
+        # colour-ordered rows have a fixed update order: A x and A^T x agree bit for bit
+        np.testing.assert_array_equal(h.run(x, "color", False), h.run(x, "color", True))
+        for s in ("window", "atomic"):
+            y1, y2 = h.run(x, s, False), h.run(x, s, True)
+            _check(m, x, y1, False, TOL["f64"])
+            assert oracle.max_rel_err(m, x, y1, y2) <= 1e-12
+    finally:
+        h.close()
+
+
+# --------------------------------------------------------------------------- interface behaviour
+def test_host_pointers_are_staged(cs):
+    m = fe.p1_grid(50, 40, 9)
+    x = fe.source_vector(m.n, 10)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        y = np.full(m.n, np.nan)
+        cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, None)
+        torch.cuda.synchronize()
+        _check(m, x, y, False, TOL["f64"])
+        xp = torch.from_numpy(x).pin_memory()
+        yp = torch.empty_like(xp).pin_memory()
+        cs.csrc_spmv_t(h, xp, yp, cs.CSRC_STRAT_AUTO, None)
+        torch.cuda.synchronize()
+        _check(m, x, yp.numpy(), True, TOL["f64"])
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_interface_errors(cs):
+    m = fe.p1_grid(10, 10, 1)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        xd = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(cs.CsrcError) as e:
+            cs.csrc_spmv(h, xd, xd, cs.CSRC_STRAT_WINDOW)
+        assert e.value.status == cs.CSRC_ERR_ALIAS
+        with pytest.raises(cs.CsrcError) as e:
+            cs.csrc_spmv(h, xd, torch.zeros_like(xd), cs.CSRC_STRAT_COLOR)
+        assert e.value.status == cs.CSRC_ERR_NOT_COLORED
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_double_float_range_is_reported(cs):
+    m = fe.p1_grid(20, 20, 2)
+    x = fe.source_vector(m.n, 3)
+    x[17] = 1e300
+    h = Handle(cs, m)
+    try:
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        cs.csrc_spmv(h.h, xd, yd, cs.CSRC_STRAT_WINDOW)
+        torch.cuda.synchronize()
+        assert cs.csrc_get_last_device_error(h.h) == cs.CSRC_ERR_RANGE
+        assert cs.csrc_get_last_device_error(h.h) == cs.CSRC_OK  # cleared by the read
+    finally:
+        h.close()
+    # FP64-pipe arithmetic handles the full double range
+    h = Handle(cs, m, flags=cs.CSRC_FLAG_FP64_ARITH)
+    try:
+        _check(m, x, h.run(x, "window"), False, TOL["f64"])
+    finally:
+        h.close()
+    # matrix values outside the double-float range switch the handle to FP64 arithmetic
+    m2 = fe.FEMatrix(m.n, m.row_ptr, m.col, m.val * 1e-30)
+    h = Handle(cs, m2)
+    try:
+        assert cs.csrc_get_info(h.h)["arith"] == 1
+        x2 = fe.source_vector(m.n, 4)
+        _check(m2, x2, h.run(x2, "window"), False, TOL["f64"])
+    finally:
+        h.close()
+
+
+def test_degenerate_matrices(cs):
+    # diagonal only, a single row, and rows without lower entries
+    for n in (1, 5, 64, 65):
+        rp = np.arange(n + 1, dtype=np.int64)
+        col = np.arange(n, dtype=np.int32)
+        val = np.arange(1, n + 1, dtype=np.float64)
+        m = fe.FEMatrix(n, rp, col, val)
+        x = fe.source_vector(n, n)
+        xi = fe.integer_vector(n, n)
+        h = Handle(cs, m, seed=1)
+        try:
+            for s in STRATS:
+                np.testing.assert_array_equal(h.run(xi, s), val * xi)
+                _check(m, x, h.run(x, s), False, TOL["f64"])
+        finally:
+            h.close()
+    # empty matrix
+    h = cs.csrc_create_from_csr(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    cs.csrc_spmv(h, torch.zeros(1, dtype=torch.float64, device="cuda"),
+                 torch.zeros(1, dtype=torch.float64, device="cuda"))
+    cs.csrc_destroy(h)
+
+
+def test_coo_and_padding(cs):
+    m = fe.p1_grid(12, 9, 4)
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr)).astype(np.int32)
+    # COO in shuffled order with one entry split into two duplicates
+    perm = np.random.default_rng(0).permutation(m.nnz)
+    r, c, v = rows[perm], m.col[perm], m.val[perm].copy()
+    r = np.concatenate([r, r[:1]])
+    c = np.concatenate([c, c[:1]])
+    v = np.concatenate([v, [0.0]])
+    h = cs.csrc_create_from_coo(m.n, len(r), r, c, v, cs.CSRC_F64)
+    try:
+        x = fe.source_vector(m.n, 5)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        cs.csrc_spmv(h, xd, yd, cs.CSRC_STRAT_WINDOW)
+        _check(m, x, yd.cpu().numpy(), False, TOL["f64"])
+    finally:
+        cs.csrc_destroy(h)
+    # drop the upper triangle: padding adds explicit zero mirrors
+    keep = m.col <= rows
+    rp = np.zeros(m.n + 1, np.int64)
+    np.cumsum(np.bincount(rows[keep], minlength=m.n), out=rp[1:])
+    lower = fe.FEMatrix(m.n, rp, m.col[keep], m.val[keep])
+    with pytest.raises(cs.CsrcError) as e:
+        cs.csrc_create_from_csr(lower.n, lower.row_ptr, lower.col, lower.val, cs.CSRC_F64)
+    assert e.value.status == cs.CSRC_ERR_NOT_STRUCT_SYMMETRIC
+    h = cs.csrc_create_from_csr(lower.n, lower.row_ptr, lower.col, lower.val, cs.CSRC_F64, cs.CSRC_FLAG_PAD_PATTERN)
+    try:
+        x = fe.source_vector(m.n, 6)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        cs.csrc_spmv(h, xd, yd, cs.CSRC_STRAT_WINDOW)
+        yref = oracle.csr_spmv(lower.n, lower.row_ptr, lower.col, lower.val, x)
+        assert oracle.max_rel_err(lower, x, yd.cpu().numpy(), yref) <= 1e-12
+    finally:
+        cs.csrc_destroy(h)
+
+
+# --------------------------------------------------------------------------- full-size configurations
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["q1s_96", "q1v_96"])
+def test_full_size_q1(cs, name):
+    builder, xseed = fe.CONFIGS[name]
+    m = builder()
+    x = fe.source_vector(m.n, xseed)
+    yref = oracle.csr_spmv(m.n, m.row_ptr, m.col, m.val, x)
+    mt = _transpose(m) if name == "q1s_96" else None
+    h = Handle(cs, m)
+    try:
+        for strategy in ("window", "atomic"):
+            y = h.run(x, strategy)
+            err = oracle.max_rel_err(m, x, y, yref)
+            assert err <= TOL["f64"], (strategy, err)
+        if mt is not None:
+            y = h.run(x, "window", True)
+            assert oracle.max_rel_err(mt, x, y, oracle.csr_spmv(m.n, mt.row_ptr, mt.col, mt.val, x)) <= TOL["f64"]
+    finally:
+        h.close()
