@@ -1,7 +1,8 @@
 """Python binding of the GB300 CSRC library (include/csrc.h).
 
 The binding only marshals arguments. Every step of a product runs in the
-library's CUDA kernels, which ``libcsrc_gb300.so`` loads through this module.
+library's CUDA kernels in ``lib/libcsrc_gb300.so``, which this module builds in-tree
+on first import when it is missing or stale, then loads.
 PyTorch supplies device memory and streams: tensors are passed by
 ``data_ptr()``, streams by ``cuda_stream``. If the shared library is missing,
 the import fails. There is no fallback path.
@@ -86,9 +87,15 @@ SIGNATURES = {
 
 
 def _load():
+    # build in-tree when the library is missing or older than its sources
+    from . import build as _build
+
+    try:
+        _build.build()
+    except Exception as e:  # no nvcc, compile error, ...
+        raise ImportError(f"cannot build {LIB_PATH}: {e} (there is no CPU fallback)") from e
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1003_0952_gb300.build` "
-                          "(there is no CPU fallback)")
+        raise ImportError(f"{LIB_PATH} is missing (there is no CPU fallback)")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)

@@ -29,6 +29,7 @@ struct csrc_matrix_s {
   std::vector<int32_t> ia, ja;  // host copy of the structure (planning, colouring)
   int32_t* d_ia = nullptr;
   int32_t* d_ja = nullptr;
+  int32_t* d_blk_row = nullptr;  // row holding pair g * 128, g = 0 .. ceil(h/128)
   void* d_al = nullptr;
   void* d_au = nullptr;
   void* d_ad = nullptr;
@@ -402,6 +403,7 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     a.n = h->n;
     a.ia = h->d_ia;
     a.ja = h->d_ja;
+    a.blk_row = h->d_blk_row;
     a.al = g;
     a.au = sc;
     a.ad = h->d_ad;
@@ -563,6 +565,19 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return from_cuda(e);
   };
+  {
+    // row holding the first pair of every 128-pair block (band kernels search from it)
+    const int64_t nblk = (h64 + (1 << kBlockShift) - 1) >> kBlockShift;
+    std::vector<int32_t> blk((size_t)nblk + 1, std::max<int32_t>(0, n - 1));
+    int32_t r = 0;
+    for (int64_t g = 0; g < nblk; ++g) {
+      const int64_t k = g << kBlockShift;
+      while (r + 1 < n && (int64_t)ia[(size_t)r + 1] <= k) ++r;
+      blk[(size_t)g] = r;
+    }
+    if ((st = from_cuda(upload(&m->d_blk_row, blk, stream))) != CSRC_OK) return fail(st);
+    if ((st = from_cuda(cudaStreamSynchronize(stream))) != CSRC_OK) return fail(st);
+  }
   if ((st = put_values(m->d_al, al)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_ad, ad)) != CSRC_OK) return fail(st);
@@ -829,7 +844,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   ensure_device(h);
   cudaDeviceSynchronize();
   free_plan(h->plan);
-  dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
+  dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_blk_row); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   delete h;
   return CSRC_OK;

@@ -91,6 +91,17 @@ __device__ __forceinline__ void df_acc(df32& s, df32 p) {
   s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
 }
 
+// s += p for a short run of terms (a thread's few pairs of one row): TwoSum of the
+// high parts, error and low parts summed into s.lo without renormalising. The
+// atomic flush that follows renormalises the high word.
+__device__ __forceinline__ void df_acc_short(df32& s, df32 p) {
+  const float t = __fadd_rn(s.hi, p.hi);
+  const float v = __fsub_rn(t, s.hi);
+  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, v)), __fsub_rn(p.hi, v));
+  s.lo = __fadd_rn(s.lo, __fadd_rn(e, p.lo));
+  s.hi = t;
+}
+
 // Error-compensated atomic accumulation of p into the pair of FP32 cells (*whi, *wlo).
 // The atomic returns the old high word, so the rounding error of the high-word
 // addition is recovered exactly (TwoSum) and sent to the low word with p.lo.

@@ -14,6 +14,8 @@ namespace csrc {
 constexpr int kPageShift = 6;
 constexpr int kPageRows = 1 << kPageShift;
 constexpr int kBandThreads = 512;
+// Pairs per block of the row-start metadata (blk_row[g] = row holding pair g << kBlockShift).
+constexpr int kBlockShift = 7;
 
 // Arithmetic of a product.
 enum Arith : int32_t { ARITH_DF32 = 0, ARITH_F64 = 1, ARITH_F32 = 2 };
@@ -49,6 +51,7 @@ struct BandArgs {
   int32_t n;
   const int32_t* ia;
   const int32_t* ja;
+  const int32_t* blk_row;  // ceil(h / 128) + 1 entries
   const void* al;  // gathered values  (au for the transpose)
   const void* au;  // scattered values (al for the transpose)
   const void* ad;

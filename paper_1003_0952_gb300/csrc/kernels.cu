@@ -36,23 +36,47 @@ enum { MODE_DF = 0, MODE_F64 = 1, MODE_F32 = 2, MODE_BF16 = 3 };
 // ---------------------------------------------------------------------------- loads
 __device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
 
-// Load the 4 values starting at k (k % 4 == 0) of a value array of the mode's storage type.
+// The 4 stored values starting at k (k % 4 == 0), kept in their storage format.
 template <int MODE>
-__device__ __forceinline__ void load4(const void* base, int k, double (&d)[4], float (&f)[4]) {
+struct Raw4 {  // MODE_DF / MODE_F64: 32 bytes
+  double2 a, b;
+};
+template <>
+struct Raw4<MODE_F32> {
+  float4 a;
+};
+template <>
+struct Raw4<MODE_BF16> {
+  uint2 a;
+};
+
+template <int MODE>
+__device__ __forceinline__ Raw4<MODE> raw_load(const void* base, int k) {
+  Raw4<MODE> r;
   if constexpr (MODE == MODE_DF || MODE == MODE_F64) {
     const double2* p = reinterpret_cast<const double2*>(static_cast<const double*>(base) + k);
-    const double2 a = __ldcs(p);
-    const double2 b = __ldcs(p + 1);
-    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+    r.a = __ldcs(p);
+    r.b = __ldcs(p + 1);
   } else if constexpr (MODE == MODE_F32) {
-    const float4 a = __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(base) + k));
-    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    r.a = __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(base) + k));
   } else {
-    const uint2 a = __ldcs(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(base) + k));
-    f[0] = __uint_as_float(a.x << 16);
-    f[1] = __uint_as_float(a.x & 0xffff0000u);
-    f[2] = __uint_as_float(a.y << 16);
-    f[3] = __uint_as_float(a.y & 0xffff0000u);
+    r.a = __ldcs(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(base) + k));
+  }
+  return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ double raw_d(const Raw4<MODE>& r, int q) {
+  return q == 0 ? r.a.x : q == 1 ? r.a.y : q == 2 ? r.b.x : r.b.y;
+}
+
+template <int MODE>
+__device__ __forceinline__ float raw_f(const Raw4<MODE>& r, int q) {
+  if constexpr (MODE == MODE_F32) {
+    return q == 0 ? r.a.x : q == 1 ? r.a.y : q == 2 ? r.a.z : r.a.w;
+  } else {
+    const unsigned w = q < 2 ? r.a.x : r.a.y;
+    return __uint_as_float((q & 1) ? (w & 0xffff0000u) : (w << 16));
   }
 }
 
@@ -130,7 +154,7 @@ struct Acc {
 
 // ---------------------------------------------------------------------------- the band kernel
 template <int MODE, bool ATOMIC>
-__global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
+__global__ void __launch_bounds__(kBandThreads, 2) band_kernel(BandArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x + a.band_offset;
   const int r0 = a.band_row[b];
@@ -184,21 +208,37 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
   };
 
   // ---- phase 2: stream the band's pairs
+  // Each thread takes 4 consecutive pairs per step (one 16-byte ja load, 16/8-byte value
+  // loads), and the loads of the next step are issued before the current step is
+  // processed. The row of a pair is searched between the rows that start the pair's
+  // 128-pair block and the next one (blk_row, precomputed), a few rows at most.
   const int kbeg = __ldg(a.ia + r0);
   const int kend = __ldg(a.ia + r1);
   using XT = typename Acc<MODE>::X;
-  for (int kb = kbeg & ~3; kb < kend; kb += 4 * kBandThreads) {
-    const int k0 = kb + 4 * tid;
-    if (k0 >= kend) break;
-    const int4 j4 = ld_stream(reinterpret_cast<const int4*>(a.ja + k0));
-    double gd[4], sd[4];
-    float gf[4], sf[4];
-    load4<MODE>(a.al, k0, gd, gf);
-    load4<MODE>(a.au, k0, sd, sf);
-    const int jj[4] = {j4.x, j4.y, j4.z, j4.w};
+  constexpr int kStep = 4 * kBandThreads;
+  int k0 = (kbeg & ~3) + 4 * tid;
+  int4 cj = make_int4(0, 0, 0, 0);
+  Raw4<MODE> cg{}, cv{};
+  if (k0 < kend) {
+    cj = ld_stream(reinterpret_cast<const int4*>(a.ja + k0));
+    cg = raw_load<MODE>(a.al, k0);
+    cv = raw_load<MODE>(a.au, k0);
+  }
+  for (; k0 < kend; k0 += kStep) {
+    const int kn = k0 + kStep;
+    int4 nj = make_int4(0, 0, 0, 0);
+    Raw4<MODE> ng{}, nv{};
+    if (kn < kend) {
+      nj = ld_stream(reinterpret_cast<const int4*>(a.ja + kn));
+      ng = raw_load<MODE>(a.al, kn);
+      nv = raw_load<MODE>(a.au, kn);
+    }
+    const int jj[4] = {cj.x, cj.y, cj.z, cj.w};
     // row of the first pair of this thread that lies inside the band
     const int kf = k0 > kbeg ? k0 : kbeg;
-    int lo = r0, hi = r1 - 1;
+    const int blk = k0 >> kBlockShift;
+    int lo = max(__ldg(a.blk_row + blk), r0);
+    int hi = min(__ldg(a.blk_row + blk + 1), r1 - 1);
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (__ldg(a.ia + mid) <= kf) lo = mid; else hi = mid - 1;
@@ -206,9 +246,8 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
     int r = lo;
     int rend = __ldg(a.ia + r + 1);
     int rslot = slot_of(r);
-    XT xr;
     if (rslot < 0) { bad |= 4u; rslot = 0; }
-    xr = win.xs[rslot];
+    XT xr = win.xs[rslot];
     Acc<MODE> acc;
     acc.zero();
 #pragma unroll
@@ -237,9 +276,9 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
         } else {
           xj = df_split<true>(__ldg(static_cast<const double*>(a.x) + j), &bad);
         }
-        const df32 g = df_split<false>(gd[q], nullptr);
-        const df32 sv = df_split<false>(sd[q], nullptr);
-        df_acc(acc.v, df_mul(g, xj));
+        const df32 g = df_split<false>(raw_d(cg, q), nullptr);
+        const df32 sv = df_split<false>(raw_d(cv, q), nullptr);
+        df_acc_short(acc.v, df_mul(g, xj));
         const df32 p = df_mul(sv, xr);
         if (js >= 0) {
           df_atomic_add(win.whi + js, win.wlo + js, p);
@@ -250,8 +289,8 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
         }
       } else if constexpr (MODE == MODE_F64) {
         const double xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const double*>(a.x) + j);
-        acc.v = fma(gd[q], xj, acc.v);
-        const double p = sd[q] * xr;
+        acc.v = fma(raw_d(cg, q), xj, acc.v);
+        const double p = raw_d(cv, q) * xr;
         if (js >= 0) {
           atomicAdd(win.w + js, p);
         } else if (ATOMIC) {
@@ -261,8 +300,8 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
         }
       } else {
         const float xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const float*>(a.x) + j);
-        acc.v = __fmaf_rn(gf[q], xj, acc.v);
-        const float p = __fmul_rn(sf[q], xr);
+        acc.v = __fmaf_rn(raw_f<MODE>(cg, q), xj, acc.v);
+        const float p = __fmul_rn(raw_f<MODE>(cv, q), xr);
         if (js >= 0) {
           atomicAdd(win.w + js, p);
         } else if (ATOMIC) {
@@ -277,6 +316,9 @@ __global__ void __launch_bounds__(kBandThreads) band_kernel(BandArgs a) {
     } else {
       atomicAdd(win.w + rslot, acc.v);
     }
+    cj = nj;
+    cg = ng;
+    cv = nv;
   }
   __syncthreads();
 
