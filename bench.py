@@ -1,0 +1,396 @@
+"""Benchmark of the CSRC product y = A x and y = A^T x on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One step is one y = A x and one y = A^T x (Fig. 2(a), Section 5) with the
+library's window strategy: a band-kernel launch and an accumulation launch for
+each product. The default workload is the Q1 hexahedral 27-point matrix on 96^3
+nodes with 3 DOFs per node (n = 2,654,208, nnz = 210,542,904), RCM ordered,
+FP64 values, synthetic and seeded. Its 2.15 GB per product is far larger than
+L2 (129 MB), so no L2 flush is needed between steps.
+
+The metric is GB/s over the CSRC working set (ia + ja + al + au + ad + x + y,
+10 nnz + 18 n + 4 bytes per FP64 product, Table 1's ws) and its fraction of
+the measured HBM bandwidth. Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (plain single-threaded FP64 C) on a
+leading principal submatrix of the same matrix, sized so the run ends within a
+few minutes, with the same metric and unit.
+
+N > 1 (torchrun, one process per GPU) runs independent replicas: the product
+has no exchange step on one matrix per GPU, so value = the bytes all ranks
+processed / the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CSRC SpMV GB/s and % of HBM roofline (FP64 vs mixed-prec batched, 1 GB300)"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["kernels.cu", "df32.cuh", "internal.h"]
+
+
+# ----------------------------------------------------------------------------- helpers
+def model_bytes(n: int, pairs: int, value_bytes: int = 8, vec_bytes: int = 8) -> int:
+    """ia + ja + al + au + ad + x + y of one product (Table 1's ws for FP64)."""
+    return 4 * (n + 1) + 4 * pairs + 2 * value_bytes * pairs + value_bytes * n + 2 * vec_bytes * n
+
+
+def flops(n: int, pairs: int) -> int:
+    """2 nnz - n (Section 4.1): n multiplies on the diagonal and 2 multiply-adds per pair."""
+    return n + 4 * pairs
+
+
+def measured_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1003_0952_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the product kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("kernel_source_sha") == kernel_source_sha():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples taken during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(v: float, world: int, device) -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- workload
+def build_workload(name: str):
+    import fe_inputs as fe
+
+    builder, xseed = fe.CONFIGS[name]
+    m = builder()
+    x = fe.source_vector(m.n, xseed)
+    return m, x
+
+
+def describe(name: str, m) -> dict:
+    return {"workload": f"{name}: " + {
+        "q1v_96": "Q1 hex 27-point stencil, 96^3 nodes x 3 DOF (3x3 blocks), random then RCM order, "
+                  "al != au U[-1,1], FP64 values, y = A x and y = A^T x",
+        "q1s_96": "Q1 hex 27-point stencil, 96^3 nodes, scalar, random then RCM order, FP64, y = A x and y = A^T x",
+        "p1_100x100": "P1 triangles on a 100x100 node grid, natural order, FP64, y = A x and y = A^T x",
+    }.get(name, name), "n": int(m.n), "nnz": int(m.nnz), "pairs": int(m.pairs),
+        "strategy": "window (shared-memory windows + deterministic accumulation)",
+        "l2": "inputs larger than L2 (129 MB): no flush" if model_bytes(m.n, m.pairs) > 129e6
+        else "fits in L2: no flush, L2-resident figure"}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def oracle_gbs(m, x, budget_s: float, max_rows: int | None = None):
+    """Time the oracle's Fig. 2(a) product (and its transpose) on the leading
+    max_rows x max_rows principal submatrix, repeating until budget_s passes.
+    Returns (GB/s, products, seconds, rows)."""
+    import oracle
+
+    c = oracle.from_matrix(m)
+    rows = m.n if max_rows is None else min(m.n, max_rows)
+    if rows < m.n:
+        c = oracle.CSRC(rows, c.ia[:rows + 1].copy(), c.ja[:int(c.ia[rows])], c.al[:int(c.ia[rows])],
+                        c.au[:int(c.ia[rows])], c.ad[:rows])
+    xs = x[:rows]
+    nbytes = model_bytes(rows, c.pairs)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.csrc_spmv(c, xs)
+        oracle.csrc_spmv_t(c, xs)
+        done += 2
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return nbytes * done / el / 1e9, done, el, rows
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    m, x = build_workload(args.workload)
+    # calibrate: one product pair on a sample, then size each step to fit the budget
+    total_budget = 120.0
+    per_step = total_budget / max(1, args.steps + args.warmup)
+    _, _, el, rows = oracle_gbs(m, x, 0.0, max_rows=min(m.n, 200_000))
+    rows_step = int(max(1000, min(m.n, rows * per_step / max(el, 1e-6))))
+    import oracle
+
+    c = oracle.from_matrix(m)
+    c = oracle.CSRC(rows_step, c.ia[:rows_step + 1].copy(), c.ja[:int(c.ia[rows_step])],
+                    c.al[:int(c.ia[rows_step])], c.au[:int(c.ia[rows_step])], c.ad[:rows_step])
+    xs = x[:rows_step]
+    for _ in range(args.warmup):
+        oracle.csrc_spmv(c, xs)
+        oracle.csrc_spmv_t(c, xs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.csrc_spmv(c, xs)
+        oracle.csrc_spmv_t(c, xs)
+    el = time.perf_counter() - t0
+    nbytes = 2 * model_bytes(rows_step, c.pairs)
+    gbs = nbytes * args.steps / el / 1e9
+    cfg = describe(args.workload, m)
+    sample = (f"leading {rows_step}x{rows_step} principal submatrix ({c.pairs} pairs) of the workload, "
+              f"y = A x and y = A^T x per step")
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_1003_0952_gb300 as cs
+
+    m, x_np = build_workload(args.workload)
+    strategy = cs.STRATEGIES[args.strategy]
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        cs.csrc_partition(h, 0)
+        info = cs.csrc_get_info(h)
+        stream = torch.cuda.current_stream()
+        sptr = stream.cuda_stream
+        x = torch.from_numpy(x_np).to(dev)
+        y = torch.empty_like(x)
+        yt = torch.empty_like(x)
+
+        def step():
+            cs.csrc_spmv(h, x, y, strategy, sptr)
+            cs.csrc_spmv_t(h, x, yt, strategy, sptr)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        st = cs.csrc_get_last_device_error(h)
+        if st != cs.CSRC_OK:
+            raise RuntimeError(f"device status after warm-up: {cs.csrc_status_string(st)}")
+
+        # ---- timed region: device time with CUDA events on the launch stream
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.3)
+        cs.csrc_set_profiling(h, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms_local = ev0.elapsed_time(ev1)
+        ktimes = cs.csrc_get_kernel_times(h)
+        cs.csrc_set_profiling(h, False)
+        clk = clocks.stop()
+        ms = reduce_max(ms_local, world, dev)
+
+        # ---- end to end through the public API with pinned host buffers
+        xh = torch.from_numpy(x_np).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        yth = torch.empty_like(xh).pin_memory()
+
+        def step_host():
+            cs.csrc_spmv(h, xh, yh, strategy, sptr)
+            cs.csrc_spmv_t(h, xh, yth, strategy, sptr)
+            stream.synchronize()
+
+        for _ in range(3):
+            step_host()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+        barrier(world)
+        st = cs.csrc_get_last_device_error(h)
+        if st != cs.CSRC_OK:
+            raise RuntimeError(f"device status after the timed steps: {cs.csrc_status_string(st)}")
+    finally:
+        cs.csrc_destroy(h)
+
+    nbytes_step = 2 * int(info["model_bytes"])
+    value = world * nbytes_step * args.steps / (ms * 1e-3) / 1e9
+    e2e_value = world * nbytes_step * args.steps / e2e_s / 1e9
+    peak, peak_src = measured_hbm()
+    nprod, ms_prod = ktimes["product"]
+    # algorithmic bytes of one band-kernel launch: the CSRC working set plus its spill writes
+    kbytes = int(info["model_bytes"]) + 8 * int(info["spill_entries"])
+    achieved = kbytes / (ms_prod / max(nprod, 1) * 1e-3) / 1e9 if nprod else None
+    launches = sum(v[0] for v in ktimes.values())
+    if rank != 0:
+        return 0
+    cfg = describe(args.workload, m)
+    cfg.update({"nbands": info["nbands"], "spill_entries": info["spill_entries"],
+                "arith": {0: "double-float (FP32 pairs)", 1: "FP64 pipe", 2: "FP32"}[info["arith"]],
+                "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded FE pattern and values)",
+        "config": cfg,
+        "gflops": world * flops(m.n, m.pairs) * 2 * args.steps / (ms * 1e-3) / 1e9,
+        "pct_hbm_roofline": value / world / peak,
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * 8 * m.n,
+                "d2h_bytes_per_step": 2 * 8 * m.n},
+        "roofline": {"bound": "hbm", "kernel": "band_kernel (product)", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "peak_source": f"{peak_src} hbm_gbs", "traffic": ncu_traffic(args.workload),
+                     "algorithmic_bytes_per_launch": kbytes,
+                     "launch_ms": ms_prod / max(nprod, 1)},
+        "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in ktimes.items()},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        gbs, done, el, rows = oracle_gbs(m, x_np, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} full products (y = A x and y = A^T x alternating) of the "
+                                          f"workload in {el:.1f} s, single-threaded FP64 C"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="q1v_96")
+    ap.add_argument("--strategy", default="window", choices=["auto", "window", "atomic"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

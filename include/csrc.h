@@ -176,6 +176,35 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
  * fastest one as its CSRC_STRAT_AUTO choice. x and y are device scratch vectors of n elements. */
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream);
 
+/* Kernel kinds of csrc_kernel_times. */
+enum {
+  CSRC_KERNEL_PRODUCT = 0,    /* the kernels that stream the stored pairs (band, colour-row) */
+  CSRC_KERNEL_ACCUMULATE = 1, /* the kernel that folds spilled partial sums into y */
+  CSRC_KERNEL_OTHER = 2,      /* everything else the product launches */
+  CSRC_KERNEL_KINDS = 3
+};
+
+/* Device time of the kernels a handle launched while profiling was on. */
+typedef struct {
+  int64_t launches[CSRC_KERNEL_KINDS]; /* launches per kind */
+  double ms[CSRC_KERNEL_KINDS];        /* summed device time per kind, in milliseconds */
+} csrc_kernel_times;
+
+/*
+ * Turn per-launch kernel timing on (enable != 0) or off for this handle, and drop
+ * what was recorded so far. While it is on, every kernel the handle launches is
+ * bracketed by two CUDA events on the launch stream (a measurement aid; the paper
+ * has no counterpart, it counts time with CPU timers and PAPI).
+ * Errors: INVALID_ARG.
+ */
+csrc_status csrc_set_profiling(csrc_handle h, int32_t enable);
+
+/*
+ * Wait for the recorded launches, sum their device time per kernel kind into
+ * *out (host), and drop the records. Errors: INVALID_ARG, CUDA.
+ */
+csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out);
+
 /* Fill *info (host). */
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info);
 

@@ -65,6 +65,15 @@ class csrc_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+# kernel kinds (csrc_kernel_times)
+CSRC_KERNEL_PRODUCT, CSRC_KERNEL_ACCUMULATE, CSRC_KERNEL_OTHER, CSRC_KERNEL_KINDS = 0, 1, 2, 3
+KERNEL_KINDS = ("product", "accumulate", "other")
+
+
+class csrc_kernel_times(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * CSRC_KERNEL_KINDS), ("ms", ctypes.c_double * CSRC_KERNEL_KINDS)]
+
+
 # Every entry point of include/csrc.h: name -> (restype, argtypes)
 _VP = ctypes.c_void_p
 _P = ctypes.POINTER
@@ -79,6 +88,8 @@ SIGNATURES = {
     "csrc_spmm_batched": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(_VP), _P(_VP), ctypes.c_int32, ctypes.c_int32,
                                          _VP]),
     "csrc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "csrc_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "csrc_get_kernel_times": (ctypes.c_int, [_VP, _P(csrc_kernel_times)]),
     "csrc_get_info": (ctypes.c_int, [_VP, _P(csrc_info)]),
     "csrc_get_last_device_error": (ctypes.c_int, [_VP]),
     "csrc_destroy": (ctypes.c_int, [_VP]),
@@ -194,6 +205,17 @@ def csrc_spmm_batched(hs, X, Y, nrhs, transpose=False, stream=None) -> None:
 
 def csrc_autotune(h, x, y, stream=None) -> None:
     _check(_lib.csrc_autotune(h, _ptr(x), _ptr(y), _stream(stream)), "csrc_autotune")
+
+
+def csrc_set_profiling(h, enable=True) -> None:
+    _check(_lib.csrc_set_profiling(h, int(bool(enable))), "csrc_set_profiling")
+
+
+def csrc_get_kernel_times(h) -> dict:
+    """{kind: (launches, milliseconds)} for the launches recorded since profiling was turned on."""
+    t = csrc_kernel_times()
+    _check(_lib.csrc_get_kernel_times(h, ctypes.byref(t)), "csrc_get_kernel_times")
+    return {k: (int(t.launches[i]), float(t.ms[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def csrc_get_info(h) -> dict:

@@ -48,6 +48,14 @@ struct csrc_matrix_s {
   void* d_xs = nullptr;
   void* d_ys = nullptr;
   int32_t tuned = 0;
+  // kernel timing (csrc_set_profiling): CUDA events around every launch of this handle
+  bool profiling = false;
+  struct TimedLaunch {
+    int32_t kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
   size_t vbytes() const { return storage == CSRC_F64 ? 8 : (storage == CSRC_F32 ? 4 : 2); }
   size_t xbytes() const { return storage == CSRC_F64 ? 8 : 4; }
 };
@@ -343,6 +351,42 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   return CSRC_OK;
 }
 
+cudaEvent_t pooled_event(csrc_matrix_s* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Runs `launch` on stream s; with profiling on, brackets it with a pair of events.
+template <typename F>
+cudaError_t timed_launch(csrc_matrix_s* h, int32_t kind, cudaStream_t s, F&& launch) {
+  if (!h->profiling) return launch();
+  cudaEvent_t a = pooled_event(h), b = pooled_event(h);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, s);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, s);
+  if (e != cudaSuccess) return e;
+  h->timed.push_back({kind, a, b});
+  return cudaSuccess;
+}
+
+void release_timing(csrc_matrix_s* h) {
+  for (auto& t : h->timed) {
+    h->event_pool.push_back(t.start);
+    h->event_pool.push_back(t.stop);
+  }
+  h->timed.clear();
+}
+
 csrc_status ensure_device(csrc_matrix_s* h) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return CSRC_ERR_CUDA;
@@ -395,8 +439,10 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     for (int32_t c = 0; c < h->ncolors; ++c) {
       const int32_t a = h->color_ptr[c], b = h->color_ptr[c + 1];
-      CSRC_TRY(launch_color_spmv(h->arith, h->storage, b - a, h->d_color_rows + a, h->d_ia, h->d_ja, g, sc,
-                                 h->d_ad, dx, dy, s));
+      CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s, [&] {
+        return launch_color_spmv(h->arith, h->storage, b - a, h->d_color_rows + a, h->d_ia, h->d_ja, g, sc, h->d_ad,
+                                 dx, dy, s);
+      }));
     }
   } else {
     BandArgs a;
@@ -421,10 +467,13 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     a.band_offset = 0;
     const bool atomic = strat == CSRC_STRAT_ATOMIC;
     if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
-    CSRC_TRY(launch_band(h->arith, h->storage, atomic, a, h->plan.nb, h->plan.smem_bytes, s));
-    if (!atomic)
-      CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
-                                 h->plan.acc_src, h->plan.spill_buf, dy, s));
+    CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
+                          [&] { return launch_band(h->arith, h->storage, atomic, a, h->plan.nb, h->plan.smem_bytes, s); }));
+    if (!atomic && h->plan.nacc > 0)
+      CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
+        return launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
+                                 h->plan.acc_src, h->plan.spill_buf, dy, s);
+      }));
   }
   if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, s));
   return CSRC_OK;
@@ -801,6 +850,35 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
   return CSRC_OK;
 }
 
+csrc_status csrc_set_profiling(csrc_handle h, int32_t enable) {
+  if (!h) return CSRC_ERR_INVALID_ARG;
+  release_timing(h);
+  h->profiling = enable != 0;
+  return CSRC_OK;
+}
+
+csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out) {
+  if (!h || !out) return CSRC_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  CSRC_TRY_S(ensure_device(h));
+  csrc_status st = CSRC_OK;
+  for (auto& t : h->timed) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(t.stop);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.start, t.stop);
+    if (e != cudaSuccess) {
+      st = from_cuda(e);
+      break;
+    }
+    if (t.kind >= 0 && t.kind < CSRC_KERNEL_KINDS) {
+      out->launches[t.kind] += 1;
+      out->ms[t.kind] += ms;
+    }
+  }
+  release_timing(h);
+  return st;
+}
+
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   if (!h || !info) return CSRC_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
@@ -846,6 +924,8 @@ csrc_status csrc_destroy(csrc_handle h) {
   free_plan(h->plan);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_blk_row); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
+  release_timing(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   delete h;
   return CSRC_OK;
 }
