@@ -172,6 +172,41 @@ csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy str
 csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
                               int32_t nrhs, int32_t transpose, cudaStream_t stream);
 
+/* Capacity of the fixed spill array that csrc_spmv_noalloc uses: 2^21 values (16 MiB). */
+#define CSRC_NOALLOC_MAX_SPILL_ENTRIES (1 << 21)
+
+/*
+ * y = A x (transpose == 0) or y = A^T x (transpose != 0) with the window strategy,
+ * allocating no memory. The paper has no counterpart: this entry point serves callers
+ * that may not allocate device memory while they compute, such as code whose GPU
+ * memory belongs to another allocator's pool, or host threads that must not block on
+ * the device synchronisation that cudaMalloc and cudaFree can cause. Such a caller
+ * creates its handle and calls csrc_partition once at set-up, then uses this call.
+ *
+ * It computes what csrc_spmv / csrc_spmv_t compute with CSRC_STRAT_WINDOW, with the
+ * same kernels. The only difference is that the spilled partial sums go to a fixed
+ * array of CSRC_NOALLOC_MAX_SPILL_ENTRIES values that the library holds in static
+ * device memory (16 MiB on every GPU that loads the library, kept until the process
+ * exits), instead of the buffer the handle allocates.
+ *   h          a handle on which csrc_partition has succeeded (the plan is not built here)
+ *   x, y       device pointers to n elements (double for CSRC_F64 storage, else float),
+ *              caller-owned, not overlapping; y is overwritten
+ *   transpose  0 for A x, non-zero for A^T x
+ *   stream     asynchronous on this stream
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current. Make that first call before any
+ * stream capture.
+ * Sharing: every call on a device, from any handle, uses the same array, which keeps
+ * the last call's contents. The band kernel writes every slot the accumulation reads,
+ * so nothing needs clearing between calls, but calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Errors: INVALID_ARG (null argument, host pointer, or a plan whose spill needs more
+ * than CSRC_NOALLOC_MAX_SPILL_ENTRIES values: csrc_info.spill_entries tells in
+ * advance), ALIAS, NOT_PARTITIONED (no plan yet, or a plan that cannot run the window
+ * strategy), CUDA.
+ */
+csrc_status csrc_spmv_noalloc(csrc_handle h, const void* x, void* y, int32_t transpose, cudaStream_t stream);
+
 /* Time the strategies on this handle (stream-ordered, synchronous) and keep the
  * fastest one as its CSRC_STRAT_AUTO choice. x and y are device scratch vectors of n elements. */
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream);

@@ -87,6 +87,7 @@ SIGNATURES = {
     "csrc_spmv_t": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "csrc_spmm_batched": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(_VP), _P(_VP), ctypes.c_int32, ctypes.c_int32,
                                          _VP]),
+    "csrc_spmv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "csrc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "csrc_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "csrc_get_kernel_times": (ctypes.c_int, [_VP, _P(csrc_kernel_times)]),
@@ -201,6 +202,14 @@ def csrc_spmm_batched(hs, X, Y, nrhs, transpose=False, stream=None) -> None:
     yarr = (_VP * max(b, 1))(*[_ptr(y) for y in Y])
     _check(_lib.csrc_spmm_batched(harr, b, xarr, yarr, int(nrhs), int(bool(transpose)), _stream(stream)),
            "csrc_spmm_batched")
+
+
+CSRC_NOALLOC_MAX_SPILL_ENTRIES = 1 << 21
+
+
+def csrc_spmv_noalloc(h, x, y, transpose=False, stream=None) -> None:
+    """Window-strategy product that allocates nothing (spill in the library's static array)."""
+    _check(_lib.csrc_spmv_noalloc(h, _ptr(x), _ptr(y), int(bool(transpose)), _stream(stream)), "csrc_spmv_noalloc")
 
 
 def csrc_autotune(h, x, y, stream=None) -> None:

@@ -649,6 +649,54 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
 
 }  // namespace
 
+namespace csrc {
+
+int32_t handle_device(const csrc_matrix_s* h) { return h->device; }
+
+// Window-strategy product whose spilled partial sums go to caller-provided device
+// memory `spill` (capacity in elements of the vector type). It allocates nothing:
+// the handle must already hold a window plan that covers every scatter target,
+// and x, y must be device pointers. The device of the handle must be current.
+csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool transpose, void* spill,
+                                int64_t capacity, cudaStream_t s) {
+  if (!h || !x || !y || !spill) return CSRC_ERR_INVALID_ARG;
+  if (h->n == 0) return CSRC_OK;
+  const size_t vb = (size_t)h->n * h->xbytes();
+  const char* xa = static_cast<const char*>(x);
+  const char* ya = static_cast<const char*>(y);
+  if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
+  if (!h->have_plan || !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
+  if (h->plan.spill > capacity) return CSRC_ERR_INVALID_ARG;
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
+  BandArgs a;
+  a.n = h->n;
+  a.ia = h->d_ia;
+  a.ja = h->d_ja;
+  a.blk_row = h->d_blk_row;
+  a.al = transpose ? h->d_au : h->d_al;
+  a.au = transpose ? h->d_al : h->d_au;
+  a.ad = h->d_ad;
+  a.x = x;
+  a.y = y;
+  a.band_row = h->plan.band_row;
+  a.band_plo = h->plan.band_plo;
+  a.band_ntab = h->plan.band_ntab;
+  a.band_wp = h->plan.band_wp;
+  a.wpage = h->plan.wpage;
+  a.wbase = h->plan.wbase;
+  a.wmask = h->plan.wmask;
+  a.spill = spill;
+  a.status = h->d_status;
+  a.band_offset = 0;
+  CSRC_TRY(launch_band(h->arith, h->storage, false, a, h->plan.nb, h->plan.smem_bytes, s));
+  if (h->plan.nacc > 0)
+    CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
+                               h->plan.acc_src, spill, y, s));
+  return CSRC_OK;
+}
+
+}  // namespace csrc
+
 extern "C" {
 
 csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,

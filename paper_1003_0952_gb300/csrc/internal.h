@@ -80,6 +80,11 @@ cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, const int3
                               cudaStream_t s);
 cudaError_t prepare_band_kernels(int max_smem_bytes);
 
+// Product into caller-provided spill memory, allocating nothing (api.cpp; used by noalloc.cu).
+int32_t handle_device(const csrc_matrix_s* h);
+csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool transpose, void* spill,
+                                int64_t capacity, cudaStream_t s);
+
 // Colouring (color.cu).
 cudaError_t launch_jp_round(int32_t n, const int32_t* ia, const int32_t* ja, const int32_t* up_ptr,
                             const int32_t* up, uint64_t seed, int32_t round, int32_t* state,
