@@ -264,13 +264,14 @@ def run_ours(args):
 
     m, x_np = build_workload(args.workload)
     strategy = cs.STRATEGIES[args.strategy]
-    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[args.storage])
     try:
         cs.csrc_partition(h, 0)
         info = cs.csrc_get_info(h)
         stream = torch.cuda.current_stream()
         sptr = stream.cuda_stream
-        x = torch.from_numpy(x_np).to(dev)
+        vdt = torch.float64 if args.storage == "f64" else torch.float32
+        x = torch.from_numpy(x_np).to(dev).to(vdt)
         y = torch.empty_like(x)
         yt = torch.empty_like(x)
 
@@ -307,7 +308,7 @@ def run_ours(args):
         ms = reduce_max(ms_local, world, dev)
 
         # ---- end to end through the public API with pinned host buffers
-        xh = torch.from_numpy(x_np).pin_memory()
+        xh = torch.from_numpy(x_np).to(vdt).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
         yth = torch.empty_like(xh).pin_memory()
 
@@ -336,7 +337,8 @@ def run_ours(args):
     peak, peak_src = measured_hbm()
     nprod, ms_prod = ktimes["product"]
     # algorithmic bytes of one band-kernel launch: the CSRC working set plus its spill writes
-    kbytes = int(info["model_bytes"]) + 8 * int(info["spill_entries"])
+    vec_bytes = 8 if args.storage == "f64" else 4
+    kbytes = int(info["model_bytes"]) + vec_bytes * int(info["spill_entries"])
     achieved = kbytes / (ms_prod / max(nprod, 1) * 1e-3) / 1e9 if nprod else None
     launches = sum(v[0] for v in ktimes.values())
     if rank != 0:
@@ -348,12 +350,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded FE pattern and values)",
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage if args.storage == "f64" else f"{args.storage} storage, f32 compute",
+        "data": "synthetic (seeded FE pattern and values)",
         "config": cfg,
         "gflops": world * flops(m.n, m.pairs) * 2 * args.steps / (ms * 1e-3) / 1e9,
         "pct_hbm_roofline": value / world / peak,
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * 8 * m.n,
-                "d2h_bytes_per_step": 2 * 8 * m.n},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * xh.element_size() * m.n,
+                "d2h_bytes_per_step": 2 * xh.element_size() * m.n},
         "roofline": {"bound": "hbm", "kernel": "band_kernel (product)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "peak_source": f"{peak_src} hbm_gbs", "traffic": ncu_traffic(args.workload),
@@ -384,6 +387,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="q1v_96")
     ap.add_argument("--strategy", default="window", choices=["auto", "window", "atomic"])
+    ap.add_argument("--storage", default="f64", choices=["f64", "f32", "bf16"],
+                    help="value storage: f64 (the default workload), or f32 / bf16 with float vectors")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -29,7 +29,6 @@ struct csrc_matrix_s {
   std::vector<int32_t> ia, ja;  // host copy of the structure (planning, colouring)
   int32_t* d_ia = nullptr;
   int32_t* d_ja = nullptr;
-  int32_t* d_blk_row = nullptr;  // row holding pair g * 128, g = 0 .. ceil(h/128)
   void* d_al = nullptr;
   void* d_au = nullptr;
   void* d_ad = nullptr;
@@ -39,7 +38,6 @@ struct csrc_matrix_s {
   DevPlan plan;
   bool have_plan = false;
   bool plan_covers = false;   // every scatter target lies in its band's window
-  int32_t smem_budget = 0;    // bytes of dynamic shared memory per band
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -98,6 +96,7 @@ void free_plan(DevPlan& p) {
   dfree(p.band_row); dfree(p.band_plo); dfree(p.band_ntab); dfree(p.band_wp);
   dfree(p.wpage); dfree(p.wbase); dfree(p.wmask);
   dfree(p.acc_row); dfree(p.acc_ptr); dfree(p.acc_src); dfree(p.spill_buf);
+  dfree(p.band_stage); dfree(p.stage_k); dfree(p.stage_r);
   p = DevPlan();
 }
 
@@ -156,19 +155,57 @@ void nnz_partition(const std::vector<int32_t>& ia, int32_t a, int32_t b, int32_t
 
 struct HostPlan {
   std::vector<int32_t> band_row{0}, band_plo, band_ntab, band_wp{0}, wpage, wbase;
+  std::vector<int32_t> band_stage{0}, stage_k, stage_r;
   std::vector<uint64_t> wmask;
   int32_t max_slots = 0, max_tab = 0, smem = 0;
   int64_t spill = 0;
   bool covers = true;
 };
 
+// Ring stages of band [r0, r1) for the band kernel: consecutive rows, at most `rows`
+// of them and at most `cap` pairs per stage. A row that does not fit in what is left
+// of a stage is cut there and continues in the next one. With `out` null, only counts.
+// Otherwise appends each stage's first pair and first row, then the band's end
+// (ia[r1], r1), and closes the band in band_stage. Returns the number of stages.
+int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int32_t rows, int32_t cap,
+                     HostPlan* out) {
+  int64_t k = ia[r0];
+  int32_t r = r0;
+  const int64_t kend = ia[r1];
+  int32_t count = 0;
+  while (k < kend) {
+    while (ia[(size_t)r + 1] <= k) ++r;  // the row holding pair k
+    const int64_t ks = k;
+    if (out) {
+      out->stage_k.push_back((int32_t)ks);
+      out->stage_r.push_back(r);
+    }
+    ++count;
+    int32_t used = 0;
+    while (k < kend && used < rows) {
+      const int64_t take = std::min<int64_t>((int64_t)ia[(size_t)r + 1] - k, ks + cap - k);
+      if (take <= 0) break;
+      k += take;
+      ++used;
+      if (k < ia[(size_t)r + 1]) break;  // the row continues in the next stage
+      ++r;
+    }
+  }
+  if (out) {
+    out->stage_k.push_back((int32_t)kend);
+    out->stage_r.push_back(r1);
+    out->band_stage.push_back((int32_t)out->stage_k.size());
+  }
+  return count;
+}
+
 // Build the window plan: each partition band becomes one or more execution bands
-// whose window fits `budget` bytes (bps bytes per row slot + 2 bytes per page-table
-// entry). A band that does not fit is split at its non-zero midpoint. A single row that
-// still does not fit gets a capped window when allow_overflow (targets outside it
-// take the global-atomic path); otherwise planning fails.
-bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int32_t bps,
-                     bool allow_overflow, HostPlan& hp) {
+// whose shared memory (window of np pages, page table, ia slice and stage table, as laid
+// out by BandLayout) fits `budget` bytes. A band that does not fit is split at its
+// non-zero midpoint. A single row that still does not fit gets a capped window when
+// allow_overflow (targets outside it take the global-atomic path); otherwise planning fails.
+bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int mode,
+                     bool allow_overflow, int32_t stage_rows, int32_t stage_cap, HostPlan& hp) {
   const int32_t n = h->n;
   const std::vector<int32_t>& ia = h->ia;
   const std::vector<int32_t>& ja = h->ja;
@@ -176,8 +213,11 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
   std::vector<int32_t> page_stamp((size_t)npages + 1, -1), row_stamp((size_t)n + 1, -1);
   int32_t stamp = 0;
   std::vector<int32_t> pages;
-  auto bytes_of = [&](int64_t np, int64_t ntab) -> int64_t {
-    return ((np * kPageRows * bps + 2 * ntab) + 15) / 16 * 16;
+  const int xb = window_x_bytes(mode), ab = window_acc_bytes(mode);
+  auto bytes_of = [&](int64_t np, int64_t ntab, int32_t r0, int32_t r1, int32_t nst) -> int64_t {
+    if (np > 32767 || ntab > (1 << 24)) return INT64_MAX;
+    const int32_t st0 = (int32_t)hp.stage_k.size();
+    return BandLayout::make((int)(np * kPageRows), xb, ab, (int)ntab, r0, r1, st0, st0 + nst).end;
   };
   struct Range { int32_t a, b; };
   std::vector<Range> stack;
@@ -205,7 +245,8 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
       }
       const int32_t phi = (r1 - 1) >> kPageShift;
       int64_t ntab = (int64_t)phi - minpage + 1;
-      bool fits = bytes_of((int64_t)pages.size(), ntab) <= budget && pages.size() <= 32767;
+      const int32_t nst = build_stages(ia, r0, r1, stage_rows, stage_cap, nullptr);
+      bool fits = bytes_of((int64_t)pages.size(), ntab, r0, r1, nst) <= budget;
       if (!fits && r1 - r0 > 1) {
         std::vector<int32_t> half;
         nnz_partition(ia, r0, r1, 2, half);
@@ -221,11 +262,12 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
         hp.covers = false;
         // keep the band's own pages and the nearest target pages that fit
         const int64_t own = phi - (r0 >> kPageShift) + 1;
+        if (bytes_of(own, own, r0, r1, nst) > budget) return false;
         int64_t keep = own;
         int32_t lowest = r0 >> kPageShift;
         for (int64_t q = (int64_t)pages.size() - own - 1; q >= 0; --q) {
           const int32_t p = pages[(size_t)q];
-          if (bytes_of(keep + 1, (int64_t)phi - p + 1) > budget) break;
+          if (bytes_of(keep + 1, (int64_t)phi - p + 1, r0, r1, nst) > budget) break;
           ++keep;
           lowest = p;
         }
@@ -233,6 +275,7 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
         minpage = lowest;
         ntab = (int64_t)phi - minpage + 1;
       }
+      const int64_t used_bytes = bytes_of((int64_t)pages.size(), ntab, r0, r1, nst);
       // rows below r0 that this band writes (spill rows)
       for (int32_t k = ia[r0]; k < ia[r1]; ++k) {
         const int32_t j = ja[k];
@@ -254,9 +297,10 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
       }
       hp.band_wp.push_back((int32_t)hp.wpage.size());
       hp.band_row.push_back(r1);
+      build_stages(ia, r0, r1, stage_rows, stage_cap, &hp);
       hp.max_slots = std::max(hp.max_slots, (int32_t)pages.size() * kPageRows);
       hp.max_tab = std::max(hp.max_tab, (int32_t)ntab);
-      hp.smem = std::max(hp.smem, (int32_t)bytes_of((int64_t)pages.size(), ntab));
+      hp.smem = std::max(hp.smem, (int32_t)used_bytes);
     }
   }
   if (hp.band_row.size() == 1) hp.band_row.push_back(0);  // n == 0
@@ -283,12 +327,17 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   }
   std::vector<int32_t> part;
   nnz_partition(h->ia, 0, h->n, nb, part);
-  const int32_t bps = (h->storage == CSRC_F64) ? 16 : 8;
+  const int mode = mode_of(h->arith, h->storage);
+  const int32_t budget = band_smem_limit(mode) - band_ring_bytes(mode);  // everything after the ring
+  // lanes per row: the smallest G whose T/G rows of average length fill at most one stage
+  const double avg = h->n > 0 ? (double)h->h / (double)h->n : 0.0;
+  int32_t group = 1;
+  while (group < 8 && (double)(kBandThreads / group) * avg > (double)kStageCap) group *= 2;
   HostPlan hp;
-  bool ok = build_host_plan(h, part, h->smem_budget, bps, false, hp);
+  bool ok = build_host_plan(h, part, budget, mode, false, kBandThreads / group, kStageCap, hp);
   if (!ok) {
     hp = HostPlan();
-    ok = build_host_plan(h, part, h->smem_budget, bps, true, hp);
+    ok = build_host_plan(h, part, budget, mode, true, kBandThreads / group, kStageCap, hp);
     if (!ok) return CSRC_ERR_NOT_PARTITIONED;
   }
   // accumulation map: group spill entries by row (stable: band order)
@@ -337,13 +386,20 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   CSRC_TRY(upload(&p.acc_row, acc_row, s));
   CSRC_TRY(upload(&p.acc_ptr, acc_ptr, s));
   CSRC_TRY(upload(&p.acc_src, acc_src, s));
+  hp.stage_k.resize(hp.stage_k.size() + kMetaPad, 0);  // rounded-up bulk copies read past the end
+  hp.stage_r.resize(hp.stage_r.size() + kMetaPad, 0);
+  CSRC_TRY(upload(&p.band_stage, hp.band_stage, s));
+  CSRC_TRY(upload(&p.stage_k, hp.stage_k, s));
+  CSRC_TRY(upload(&p.stage_r, hp.stage_r, s));
   CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * h->xbytes())));
   CSRC_TRY(cudaStreamSynchronize(s));
   p.spill = hp.spill;
+  p.group = group;
+  p.nstages = (int64_t)hp.stage_k.size() - kMetaPad - (int64_t)(hp.band_stage.size() - 1);
   p.nacc = (int64_t)acc_row.size();
   p.max_slots = hp.max_slots;
   p.max_tab = hp.max_tab;
-  p.smem_bytes = hp.smem;
+  p.smem_bytes = band_ring_bytes(mode) + hp.smem;
   p.total_pages = (int64_t)hp.wpage.size();
   h->part = part;
   h->have_plan = true;
@@ -403,6 +459,36 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Arguments of one band-kernel launch: the handle's arrays and plan, al and au swapped
+// for the transpose (Section 5).
+BandArgs band_args(const csrc_matrix_s* h, bool transpose, const void* x, void* y, void* spill) {
+  BandArgs a;
+  a.n = h->n;
+  a.ia = h->d_ia;
+  a.ja = h->d_ja;
+  a.band_stage = h->plan.band_stage;
+  a.stage_k = h->plan.stage_k;
+  a.stage_r = h->plan.stage_r;
+  a.group = h->plan.group;
+  a.al = transpose ? h->d_au : h->d_al;  // gathered values
+  a.au = transpose ? h->d_al : h->d_au;  // scattered values
+  a.ad = h->d_ad;
+  a.x = x;
+  a.y = y;
+  a.band_row = h->plan.band_row;
+  a.band_plo = h->plan.band_plo;
+  a.band_ntab = h->plan.band_ntab;
+  a.band_wp = h->plan.band_wp;
+  a.wpage = h->plan.wpage;
+  a.wbase = h->plan.wbase;
+  a.wmask = h->plan.wmask;
+  a.spill = spill;
+  a.status = h->d_status;
+  a.band_offset = 0;
+  a.x_bulk = (reinterpret_cast<uintptr_t>(x) & 15u) == 0u;
+  return a;
+}
+
 csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st, cudaStream_t s, bool transpose) {
   if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
   if (st < CSRC_STRAT_AUTO || st > CSRC_STRAT_ATOMIC) return CSRC_ERR_INVALID_ARG;
@@ -445,26 +531,7 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
       }));
     }
   } else {
-    BandArgs a;
-    a.n = h->n;
-    a.ia = h->d_ia;
-    a.ja = h->d_ja;
-    a.blk_row = h->d_blk_row;
-    a.al = g;
-    a.au = sc;
-    a.ad = h->d_ad;
-    a.x = dx;
-    a.y = dy;
-    a.band_row = h->plan.band_row;
-    a.band_plo = h->plan.band_plo;
-    a.band_ntab = h->plan.band_ntab;
-    a.band_wp = h->plan.band_wp;
-    a.wpage = h->plan.wpage;
-    a.wbase = h->plan.wbase;
-    a.wmask = h->plan.wmask;
-    a.spill = h->plan.spill_buf;
-    a.status = h->d_status;
-    a.band_offset = 0;
+    const BandArgs a = band_args(h, transpose, dx, dy, h->plan.spill_buf);
     const bool atomic = strat == CSRC_STRAT_ATOMIC;
     if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
@@ -556,7 +623,6 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   cudaGetDevice(&m->device);
   cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   if (m->sms <= 0) m->sms = 1;
-  m->smem_budget = 100 * 1024;
   if (storage == CSRC_F64) {
     m->arith = (flags & CSRC_FLAG_FP64_ARITH) ? ARITH_F64 : ARITH_DF32;
     // the double-float path needs values in [2^-50, 2^63) (or zero); otherwise use FP64 arithmetic
@@ -580,9 +646,12 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
     csrc_destroy(m);
     return s;
   };
-  const size_t hcap = ((size_t)h64 + 3) / 4 * 4 + 4;  // 16-byte vector loads may read past h
+  // aligned bulk copies of the band kernels may read up to the next multiple of kPairAlign pairs
+  const size_t hcap = ((size_t)h64 + kPairAlign - 1) / kPairAlign * kPairAlign + kPairAlign;
   const size_t vb = m->vbytes();
-  if (from_cuda(dmalloc(&m->d_ia, (size_t)n + 1)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  // ia is padded: the band kernels copy row-pointer slices rounded up to 4 entries
+  if (from_cuda(dmalloc(&m->d_ia, (size_t)n + 1 + kMetaPad)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if ((st = from_cuda(cudaMemsetAsync(m->d_ia, 0, ((size_t)n + 1 + kMetaPad) * 4, stream))) != CSRC_OK) return fail(st);
   if (from_cuda(dmalloc(&m->d_ja, hcap)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if (cudaMalloc(&m->d_al, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if (cudaMalloc(&m->d_au, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
@@ -614,19 +683,6 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return from_cuda(e);
   };
-  {
-    // row holding the first pair of every 128-pair block (band kernels search from it)
-    const int64_t nblk = (h64 + (1 << kBlockShift) - 1) >> kBlockShift;
-    std::vector<int32_t> blk((size_t)nblk + 1, std::max<int32_t>(0, n - 1));
-    int32_t r = 0;
-    for (int64_t g = 0; g < nblk; ++g) {
-      const int64_t k = g << kBlockShift;
-      while (r + 1 < n && (int64_t)ia[(size_t)r + 1] <= k) ++r;
-      blk[(size_t)g] = r;
-    }
-    if ((st = from_cuda(upload(&m->d_blk_row, blk, stream))) != CSRC_OK) return fail(st);
-    if ((st = from_cuda(cudaStreamSynchronize(stream))) != CSRC_OK) return fail(st);
-  }
   if ((st = put_values(m->d_al, al)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_ad, ad)) != CSRC_OK) return fail(st);
@@ -636,7 +692,7 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   {
     std::lock_guard<std::mutex> lk(g_setup_mutex);
     if (!g_prepared) {
-      if (prepare_band_kernels(227 * 1024) != cudaSuccess) {
+      if (prepare_band_kernels() != cudaSuccess) {
         cudaGetLastError();
         return fail(CSRC_ERR_CUDA);
       }
@@ -668,26 +724,7 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   if (!h->have_plan || !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
   if (h->plan.spill > capacity) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
-  BandArgs a;
-  a.n = h->n;
-  a.ia = h->d_ia;
-  a.ja = h->d_ja;
-  a.blk_row = h->d_blk_row;
-  a.al = transpose ? h->d_au : h->d_al;
-  a.au = transpose ? h->d_al : h->d_au;
-  a.ad = h->d_ad;
-  a.x = x;
-  a.y = y;
-  a.band_row = h->plan.band_row;
-  a.band_plo = h->plan.band_plo;
-  a.band_ntab = h->plan.band_ntab;
-  a.band_wp = h->plan.band_wp;
-  a.wpage = h->plan.wpage;
-  a.wbase = h->plan.wbase;
-  a.wmask = h->plan.wmask;
-  a.spill = spill;
-  a.status = h->d_status;
-  a.band_offset = 0;
+  const BandArgs a = band_args(h, transpose, x, y, spill);
   CSRC_TRY(launch_band(h->arith, h->storage, false, a, h->plan.nb, h->plan.smem_bytes, s));
   if (h->plan.nacc > 0)
     CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
@@ -970,7 +1007,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   ensure_device(h);
   cudaDeviceSynchronize();
   free_plan(h->plan);
-  dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_blk_row); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
+  dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);

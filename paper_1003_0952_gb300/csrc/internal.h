@@ -13,12 +13,98 @@ namespace csrc {
 // Rows per window page (page table granularity, one 64-bit spill mask per page).
 constexpr int kPageShift = 6;
 constexpr int kPageRows = 1 << kPageShift;
+
+
+// Stored arrays (ja, al, au) are padded so that 8-pair aligned bulk copies stay inside them.
+constexpr int kPairAlign = 8;
+
+// Kernel modes (storage x arithmetic).
+enum { MODE_DF = 0, MODE_F64 = 1, MODE_F32 = 2, MODE_BF16 = 3 };
+
+// Shape of the band kernel per mode: T threads, ring stages of up to kStageCap pairs
+// (plus 16 for alignment), NS stages, CTAs per SM. A stage holds whole rows (a row longer
+// than a stage is cut), at most T/G of them, G = lanes per row (a per-matrix choice).
+// kSlotBytes = shared bytes per window row (x plus its accumulator).
+template <int MODE>
+struct BandShape {
+  static constexpr int T = 512;
+  static constexpr int kStageCap = 2560;
+  static constexpr int NS = 3;
+  static constexpr int kCtasPerSm = 1;
+  static constexpr int kValueBytes = MODE == MODE_BF16 ? 2 : (MODE == MODE_F32 ? 4 : 8);
+  static constexpr int kSlotBytes = (MODE == MODE_DF || MODE == MODE_F64) ? 16 : 8;
+  static constexpr int kSlotPairs = kStageCap + 16;
+  static constexpr int ring_bytes() { return NS * kSlotPairs * (4 + 2 * kValueBytes); }
+};
 constexpr int kBandThreads = 512;
-// Pairs per block of the row-start metadata (blk_row[g] = row holding pair g << kBlockShift).
-constexpr int kBlockShift = 7;
+constexpr int kStageCap = 2560;
+
+// Shared memory ahead of the ring (mbarriers: NS full, NS empty, one for the band's set-up copies).
+constexpr int kRingOffset = 128;
+
+// Dynamic shared memory a band CTA may use, per mode (a little below the per-CTA maximum
+// for its CTAs-per-SM target, leaving room for static shared variables).
+constexpr int kSmemPerSm = 233472;   // 228 KB on sm_103
+constexpr int kSmemPerCtaMax = 232448;  // 227 KB opt-in maximum
+constexpr int smem_limit_for(int ctas_per_sm) {
+  return (ctas_per_sm <= 1 ? kSmemPerCtaMax : kSmemPerSm / ctas_per_sm - 1024) - 256;
+}
+inline int band_smem_limit(int mode) {
+  switch (mode) {
+    case MODE_DF: return smem_limit_for(BandShape<MODE_DF>::kCtasPerSm);
+    case MODE_F64: return smem_limit_for(BandShape<MODE_F64>::kCtasPerSm);
+    case MODE_F32: return smem_limit_for(BandShape<MODE_F32>::kCtasPerSm);
+    default: return smem_limit_for(BandShape<MODE_BF16>::kCtasPerSm);
+  }
+}
+inline int band_ring_bytes(int mode) {
+  switch (mode) {
+    case MODE_DF: return kRingOffset + BandShape<MODE_DF>::ring_bytes();
+    case MODE_F64: return kRingOffset + BandShape<MODE_F64>::ring_bytes();
+    case MODE_F32: return kRingOffset + BandShape<MODE_F32>::ring_bytes();
+    default: return kRingOffset + BandShape<MODE_BF16>::ring_bytes();
+  }
+}
+
+// Layout of a band's shared memory after the ring, identical on host and device:
+// [x of the window slots][window sums][page table][ia slice][stage_k slice][stage_r slice].
+// The ia slice covers rows [r0 & ~3, (r1 + 4) & ~3), the stage slices cover stage entries
+// [st0 & ~3, (st1 + 4) & ~3) where st1 = index of the band's end entry; each part is a
+// multiple of 16 bytes so that it can be filled by bulk copies.
+struct BandLayout {
+  int xs, acc, tab, ia, sk, sr, end;  // byte offsets from the ring's end
+  static constexpr int up16(int v) { return (v + 15) & ~15; }
+  __host__ __device__ static BandLayout make(int nslots, int x_bytes, int acc_bytes, int ntab, int r0, int r1,
+                                             int st0, int st1) {
+    BandLayout l;
+    l.xs = 0;
+    l.acc = nslots * x_bytes;
+    l.tab = l.acc + nslots * acc_bytes;
+    l.ia = l.tab + up16(4 * ntab);
+    const int nia = ((r1 + 4) & ~3) - (r0 & ~3);
+    l.sk = l.ia + 4 * nia;
+    const int nst = ((st1 + 4) & ~3) - (st0 & ~3);
+    l.sr = l.sk + 4 * nst;
+    l.end = l.sr + 4 * nst;
+    return l;
+  }
+};
+// Bytes per window slot of x and of the sums, per mode.
+constexpr int window_x_bytes(int mode) { return (mode == MODE_DF || mode == MODE_F64) ? 8 : 4; }
+constexpr int window_acc_bytes(int mode) { return (mode == MODE_DF || mode == MODE_F64) ? 8 : 4; }
+// Padding (in entries) after ia and the stage arrays, so the rounded-up slices stay inside.
+constexpr int kMetaPad = 8;
+
+inline int band_slot_bytes(int mode) { return (mode == MODE_DF || mode == MODE_F64) ? 16 : 8; }
 
 // Arithmetic of a product.
 enum Arith : int32_t { ARITH_DF32 = 0, ARITH_F64 = 1, ARITH_F32 = 2 };
+
+inline int mode_of(Arith arith, int storage) {
+  if (storage == CSRC_F32) return MODE_F32;
+  if (storage == CSRC_BF16) return MODE_BF16;
+  return arith == ARITH_F64 ? MODE_F64 : MODE_DF;
+}
 
 // Device arrays of one execution plan of the window / atomic strategies.
 // A plan is a list of row bands. Band b covers rows [band_row[b], band_row[b+1]).
@@ -26,6 +112,11 @@ enum Arith : int32_t { ARITH_DF32 = 0, ARITH_F64 = 1, ARITH_F32 = 2 };
 // indexed through a page table that spans pages [band_plo[b], band_plo[b] + band_ntab[b]).
 struct DevPlan {
   int32_t nb = 0;
+  int32_t group = 1;             // lanes per row (1, 2, 4 or 8)
+  int64_t nstages = 0;           // ring stages over all bands
+  int32_t* band_stage = nullptr; // nb+1: stages of band b are [band_stage[b], band_stage[b+1]-1)
+  int32_t* stage_k = nullptr;    // first pair of each stage (the band's last entry is its end)
+  int32_t* stage_r = nullptr;    // first row of each stage
   int32_t* band_row = nullptr;   // nb+1
   int32_t* band_plo = nullptr;   // nb
   int32_t* band_ntab = nullptr;  // nb
@@ -42,7 +133,7 @@ struct DevPlan {
   void* spill_buf = nullptr;     // spill values (double or float)
   int32_t max_slots = 0;
   int32_t max_tab = 0;
-  int32_t smem_bytes = 0;
+  int32_t smem_bytes = 0;      // dynamic shared memory of a band CTA (ring + window + table)
   int64_t total_pages = 0;
 };
 
@@ -51,7 +142,11 @@ struct BandArgs {
   int32_t n;
   const int32_t* ia;
   const int32_t* ja;
-  const int32_t* blk_row;  // ceil(h / 128) + 1 entries
+  const int32_t* band_stage;
+  const int32_t* stage_k;
+  const int32_t* stage_r;
+  int32_t group;  // lanes per row
+  int32_t x_bulk; // x is 16-byte aligned: window pages of x are fetched with bulk copies
   const void* al;  // gathered values  (au for the transpose)
   const void* au;  // scattered values (al for the transpose)
   const void* ad;
@@ -78,7 +173,7 @@ cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandA
 cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, const int32_t* acc_row,
                               const int32_t* acc_ptr, const int32_t* acc_src, const void* spill, void* y,
                               cudaStream_t s);
-cudaError_t prepare_band_kernels(int max_smem_bytes);
+cudaError_t prepare_band_kernels();
 
 // Product into caller-provided spill memory, allocating nothing (api.cpp; used by noalloc.cu).
 int32_t handle_device(const csrc_matrix_s* h);

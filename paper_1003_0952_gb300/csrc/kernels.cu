@@ -1,27 +1,35 @@
 // Band kernels of the CSRC product y = A x (Fig. 2(a)) for sm_103a.
 //
-// One CTA runs one row band [r0, r1) of the window plan. It streams the band's
-// contiguous slice [ia[r0], ia[r1]) of ja / al / au with coalesced 16-byte
-// loads, four pairs per thread per step. Every pair gathers al*x[j] into its
-// row's register accumulator and scatters au*x[i] into y[j].
+// One CTA runs one row band [r0, r1) of the window plan. The band's stored
+// pairs are the contiguous slice [ia[r0], ia[r1]) of ja / al / au. They are
+// streamed into a ring of shared-memory stages by TMA bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per stage), issued by one
+// thread while the others compute. A stage holds whole consecutive rows (the
+// host cuts the band into stages; a row longer than a stage is cut too). Each
+// row of a stage is taken by a group of G lanes that stride through its pairs,
+// so a row's gathered sum stays in registers until the row ends.
 //
-// The scatter goes to a private window in shared memory, the GPU form of the
-// local buffers of Section 3.1. The window holds the rows this band writes: its
-// own rows and every row ja reaches below r0 (the band's "effective range"),
-// kept at 64-row page granularity and found through a page table. x for those
-// rows is staged in the same window, so gathers read shared memory too. When
-// the stream ends:
+// Every pair k of row i gathers al[k]*x[ja[k]] into row i and scatters
+// au[k]*x[i] into row ja[k]. Both land in a private window in shared memory,
+// the GPU form of the local buffers of Section 3.1: it holds the rows this
+// band writes, its own rows and every row below r0 that ja reaches (its
+// "effective range"), kept at 64-row page granularity behind a page table.
+// x for those rows is staged in the same window, so gathers read shared memory
+// too. When the stream ends:
 //  - window strategy: own rows are stored to y, and rows below r0 go to a
 //    compact spill buffer. A separate accumulation kernel folds the spills into
-//    y in fixed band order (deterministic), like the "effective" accumulation
-//    of Section 3.1.
+//    y, in band order, like the "effective" accumulation of Section 3.1.
 //  - atomic strategy: y was zeroed, and every window row is added to y with a
-//    global atomic (red.global.add, executed in L2). Pages outside the window
-//    (plans with overflow) scatter straight to y with the same atomics.
+//    global atomic (executed in L2). Pages outside the window (plans with
+//    overflow) scatter straight to y with the same atomics.
 //
 // Arithmetic by mode:
-//  - MODE_DF: FP64 storage and vectors, double-float accumulation (df32.cuh).
-//  - MODE_F64: FP64 storage, FP64-pipe arithmetic (bit-for-bit IEEE products).
+//  - MODE_DF: FP64 storage and vectors. The gather runs on the FP64 pipe (one
+//    FMA per pair, the row sum in a double register). The scatter product and the
+//    window sums use double-float arithmetic on the FP32 pipes (df32.cuh): GB300
+//    runs FP64 at a small fraction of its FP32 rate, so one FP64 operation per
+//    pair is what that pipe can take at HBM speed.
+//  - MODE_F64: FP64 storage, every operation on the FP64 pipe.
 //  - MODE_F32: FP32 storage, FP32 vectors and accumulation.
 //  - MODE_BF16: BF16 storage, FP32 vectors and accumulation.
 #include <cstdint>
@@ -31,131 +39,170 @@
 
 namespace csrc {
 
-enum { MODE_DF = 0, MODE_F64 = 1, MODE_F32 = 2, MODE_BF16 = 3 };
+// ---------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
-// ---------------------------------------------------------------------------- loads
-__device__ __forceinline__ int4 ld_stream(const int4* p) { return __ldcs(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
 
-// The 4 stored values starting at k (k % 4 == 0), kept in their storage format.
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+
+// Bounded wait for the phase with the given parity: gives up after about two
+// seconds (clock64 at ~2 GHz) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+  return true;
+}
+
+// Shared-memory reads by the generic proxy before async-proxy (TMA) writes to the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completion signalled on the mbarrier as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------- per-mode types
 template <int MODE>
-struct Raw4 {  // MODE_DF / MODE_F64: 32 bytes
-  double2 a, b;
+struct Traits;
+
+template <>
+struct Traits<MODE_DF> {
+  using V = double;  // stored value
+  using X = double;  // vector element
 };
 template <>
-struct Raw4<MODE_F32> {
-  float4 a;
+struct Traits<MODE_F64> {
+  using V = double;
+  using X = double;
 };
 template <>
-struct Raw4<MODE_BF16> {
-  uint2 a;
+struct Traits<MODE_F32> {
+  using V = float;
+  using X = float;
+};
+template <>
+struct Traits<MODE_BF16> {
+  using V = uint16_t;
+  using X = float;
 };
 
-template <int MODE>
-__device__ __forceinline__ Raw4<MODE> raw_load(const void* base, int k) {
-  Raw4<MODE> r;
-  if constexpr (MODE == MODE_DF || MODE == MODE_F64) {
-    const double2* p = reinterpret_cast<const double2*>(static_cast<const double*>(base) + k);
-    r.a = __ldcs(p);
-    r.b = __ldcs(p + 1);
-  } else if constexpr (MODE == MODE_F32) {
-    r.a = __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(base) + k));
-  } else {
-    r.a = __ldcs(reinterpret_cast<const uint2*>(static_cast<const uint16_t*>(base) + k));
-  }
-  return r;
-}
+__device__ __forceinline__ float bf16_to_f32(uint16_t v) { return __uint_as_float((unsigned)v << 16); }
 
 template <int MODE>
-__device__ __forceinline__ double raw_d(const Raw4<MODE>& r, int q) {
-  return q == 0 ? r.a.x : q == 1 ? r.a.y : q == 2 ? r.b.x : r.b.y;
-}
-
-template <int MODE>
-__device__ __forceinline__ float raw_f(const Raw4<MODE>& r, int q) {
-  if constexpr (MODE == MODE_F32) {
-    return q == 0 ? r.a.x : q == 1 ? r.a.y : q == 2 ? r.a.z : r.a.w;
+__device__ __forceinline__ float as_f32(typename Traits<MODE>::V v) {
+  if constexpr (MODE == MODE_BF16) {
+    return bf16_to_f32(v);
   } else {
-    const unsigned w = q < 2 ? r.a.x : r.a.y;
-    return __uint_as_float((q & 1) ? (w & 0xffff0000u) : (w << 16));
+    return static_cast<float>(v);
   }
 }
 
-// One stored diagonal value as the mode's element.
-template <int MODE>
-__device__ __forceinline__ float load_one_f(const void* base, int i) {
-  if constexpr (MODE == MODE_F32) {
-    return __ldg(static_cast<const float*>(base) + i);
-  } else {
-    const unsigned short v = __ldg(static_cast<const unsigned short*>(base) + i);
-    return __uint_as_float((unsigned)v << 16);
-  }
-}
-
-// ---------------------------------------------------------------------------- window views
-// Shared memory of a band: [x window][accumulator window][page table (int16)].
+// Window of a band in shared memory: x of every slot, then the accumulators.
 template <int MODE>
 struct Window;
 
 template <>
 struct Window<MODE_DF> {
-  df32* xs;
+  double* xs;
   float* whi;
   float* wlo;
-  static constexpr int kBytesPerSlot = 16;
   __device__ void bind(unsigned char* s, int nslots) {
-    xs = reinterpret_cast<df32*>(s);
+    xs = reinterpret_cast<double*>(s);
     whi = reinterpret_cast<float*>(xs + nslots);
     wlo = whi + nslots;
   }
+  __device__ void zero(int s) {
+    whi[s] = 0.f;
+    wlo[s] = 0.f;
+  }
+  __device__ double value(int s) const { return (double)whi[s] + (double)wlo[s]; }
 };
 template <>
 struct Window<MODE_F64> {
   double* xs;
   double* w;
-  static constexpr int kBytesPerSlot = 16;
   __device__ void bind(unsigned char* s, int nslots) {
     xs = reinterpret_cast<double*>(s);
     w = xs + nslots;
   }
+  __device__ void zero(int s) { w[s] = 0.0; }
+  __device__ double value(int s) const { return w[s]; }
 };
 template <int MODE>
 struct Window {  // MODE_F32 and MODE_BF16
   float* xs;
   float* w;
-  static constexpr int kBytesPerSlot = 8;
   __device__ void bind(unsigned char* s, int nslots) {
     xs = reinterpret_cast<float*>(s);
     w = xs + nslots;
   }
+  __device__ void zero(int s) { w[s] = 0.f; }
+  __device__ float value(int s) const { return w[s]; }
 };
 
-// Accumulator type and operations per mode.
+// Scatter factor x[i] of the current row, as the mode multiplies with it.
 template <int MODE>
-struct Acc;
-
-template <>
-struct Acc<MODE_DF> {
-  using X = df32;  // x element as held in registers/shared memory
-  df32 v;
-  __device__ void zero() { v.hi = 0.f; v.lo = 0.f; }
+struct RowX {
+  using type = typename Traits<MODE>::X;
 };
 template <>
-struct Acc<MODE_F64> {
-  using X = double;
-  double v;
-  __device__ void zero() { v = 0.0; }
-};
-template <int MODE>
-struct Acc {
-  using X = float;
-  float v;
-  __device__ void zero() { v = 0.f; }
+struct RowX<MODE_DF> {
+  using type = df32;
 };
 
 // ---------------------------------------------------------------------------- the band kernel
-template <int MODE, bool ATOMIC>
-__global__ void __launch_bounds__(kBandThreads, 2) band_kernel(BandArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+template <int MODE, int G, bool ATOMIC>
+__global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
+  using Sh = BandShape<MODE>;
+  using V = typename Traits<MODE>::V;
+  using X = typename Traits<MODE>::X;
+  using XR = typename RowX<MODE>::type;
+  constexpr int T = Sh::T;
+  constexpr int NS = Sh::NS;
+  constexpr int SP = Sh::kSlotPairs;  // pairs per ring slot
+  constexpr int VB = (int)sizeof(V);
+  constexpr int XB = (int)sizeof(X);
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
   const int b = blockIdx.x + a.band_offset;
   const int r0 = a.band_row[b];
   const int r1 = a.band_row[b + 1];
@@ -164,192 +211,302 @@ __global__ void __launch_bounds__(kBandThreads, 2) band_kernel(BandArgs a) {
   const int wp0 = a.band_wp[b];
   const int np = a.band_wp[b + 1] - wp0;
   const int nslots = np << kPageShift;
-  const int tid = threadIdx.x;
-  Window<MODE> win;
-  win.bind(smem, nslots);
-  short* tab = reinterpret_cast<short*>(smem + (size_t)nslots * Window<MODE>::kBytesPerSlot);
-  unsigned bad = 0u;
+  const int st0 = a.band_stage[b];
+  const int st1 = a.band_stage[b + 1] - 1;  // index of the band's end entry
+  const int nstages = st1 - st0;
 
-  // ---- phase 1: clear the page table, stage x into the window, clear the accumulators
-  for (int t = tid; t < ntab; t += kBandThreads) tab[t] = (short)-1;
-  for (int s = tid; s < nslots; s += kBandThreads) {
-    const int page = __ldg(a.wpage + wp0 + (s >> kPageShift));
-    const int j = (page << kPageShift) | (s & (kPageRows - 1));
-    if constexpr (MODE == MODE_DF) {
-      const double xv = j < a.n ? __ldg(static_cast<const double*>(a.x) + j) : 0.0;
-      win.xs[s] = df_split<true>(xv, &bad);
-      win.whi[s] = 0.f;
-      win.wlo[s] = 0.f;
-    } else if constexpr (MODE == MODE_F64) {
-      win.xs[s] = j < a.n ? __ldg(static_cast<const double*>(a.x) + j) : 0.0;
-      win.w[s] = 0.0;
-    } else {
-      win.xs[s] = j < a.n ? __ldg(static_cast<const float*>(a.x) + j) : 0.f;
-      win.w[s] = 0.f;
+  // ---- shared memory: [mbarriers][ring slots][x][sums][page table][ia][stage_k][stage_r]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // full[NS], empty[NS], setup
+  unsigned char* ring = smem + kRingOffset;
+  int32_t* ring_ja = reinterpret_cast<int32_t*>(ring);                    // [NS][SP]
+  V* ring_al = reinterpret_cast<V*>(ring + (size_t)NS * SP * 4);          // [NS][SP]
+  V* ring_au = reinterpret_cast<V*>(ring + (size_t)NS * SP * (4 + VB));   // [NS][SP]
+  unsigned char* rest = ring + Sh::ring_bytes();
+  const BandLayout L = BandLayout::make(nslots, window_x_bytes(MODE), window_acc_bytes(MODE), ntab, r0, r1, st0, st1);
+  Window<MODE> win;
+  win.bind(rest + L.xs, nslots);
+  int32_t* tab = reinterpret_cast<int32_t*>(rest + L.tab);
+  const int ia_base = r0 & ~3;
+  const int st_base = st0 & ~3;
+  const int32_t* s_ia = reinterpret_cast<const int32_t*>(rest + L.ia) - ia_base;  // s_ia[r] = ia[r]
+  const int32_t* s_sk = reinterpret_cast<const int32_t*>(rest + L.sk) - st_base;  // s_sk[st] = stage_k[st]
+  const int32_t* s_sr = reinterpret_cast<const int32_t*>(rest + L.sr) - st_base;
+
+  const uint32_t bar_full = smem_addr(bars);
+  const uint32_t bar_empty = smem_addr(bars + NS);
+  const uint32_t bar_setup = smem_addr(bars + 2 * NS);
+  // ring stage s: pairs [ks & ~7, ceil8(ke)) (16-byte aligned for every value type; the
+  // stored arrays are padded so the rounded-up end stays inside them)
+  auto issue = [&](int s, int ks, int ke) {
+    const int slot = s % NS;
+    ks &= ~(kPairAlign - 1);
+    ke = (ke + kPairAlign - 1) & ~(kPairAlign - 1);
+    const int cnt = ke - ks;  // <= kStageCap + 16 (the host caps a stage's pairs)
+    const uint32_t bar = bar_full + 8u * slot;
+    mbar_arrive_expect_tx(bar, (uint32_t)cnt * (uint32_t)(4 + 2 * VB));
+    bulk_copy_g2s(smem_addr(ring_ja + (size_t)slot * SP), a.ja + ks, (uint32_t)cnt * 4u, bar);
+    bulk_copy_g2s(smem_addr(ring_al + (size_t)slot * SP), static_cast<const V*>(a.al) + ks, (uint32_t)cnt * VB, bar);
+    bulk_copy_g2s(smem_addr(ring_au + (size_t)slot * SP), static_cast<const V*>(a.au) + ks, (uint32_t)cnt * VB, bar);
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(bar_full + 8u * i, 1u);
+      mbar_init(bar_empty + 8u * i, (uint32_t)(T / 32));
     }
+    mbar_init(bar_setup, 1u);
+    mbar_init_fence();
   }
   __syncthreads();
-  for (int q = tid; q < np; q += kBandThreads) {
-    const int t = __ldg(a.wpage + wp0 + q) - plo;
+
+  // ---- phase 1: warp 0 starts the copies (first ring stages, the band's ia slice and
+  // stage table, x of every full window page); the other warps clear the sums and build
+  // the page table meanwhile.
+  unsigned bad = 0u;
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (; issued < NS && issued < nstages; ++issued)
+        issue(issued, __ldg(a.stage_k + st0 + issued), __ldg(a.stage_k + st0 + issued + 1));
+    }
+    uint32_t bytes = 0;
+    if (lane == 0) {
+      const uint32_t nia = (uint32_t)(L.sk - L.ia), nst = (uint32_t)(L.sr - L.sk);
+      bulk_copy_g2s(smem_addr(rest + L.ia), a.ia + ia_base, nia, bar_setup);
+      bulk_copy_g2s(smem_addr(rest + L.sk), a.stage_k + st_base, nst, bar_setup);
+      bulk_copy_g2s(smem_addr(rest + L.sr), a.stage_r + st_base, nst, bar_setup);
+      bytes += nia + 2 * nst;
+    }
+    if (a.x_bulk) {
+      for (int q = lane; q < np; q += 32) {
+        const int page = __ldg(a.wpage + wp0 + q);
+        if ((page + 1) * kPageRows <= a.n) {
+          bulk_copy_g2s(smem_addr(win.xs + (q << kPageShift)), static_cast<const X*>(a.x) + (page << kPageShift),
+                        (uint32_t)(kPageRows * XB), bar_setup);
+          bytes += (uint32_t)(kPageRows * XB);
+        }
+      }
+    }
+    // every copy is issued before the one arrival that closes the phase
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    __syncwarp();
+    if (lane == 0) mbar_arrive_expect_tx(bar_setup, bytes);
+  }
+  for (int t = tid; t < ntab; t += T) tab[t] = -1;
+  for (int s = tid; s < nslots; s += T) win.zero(s);
+  __syncthreads();
+  for (int q = tid; q < np; q += T) {
+    const int page = __ldg(a.wpage + wp0 + q);
+    const int t = page - plo;
     if ((unsigned)t < (unsigned)ntab) {
-      tab[t] = (short)q;
+      tab[t] = q << kPageShift;
     } else {
       bad |= 4u;
     }
+    // pages without a bulk copy (x not 16-byte aligned, or the page runs past n)
+    if (!a.x_bulk || (page + 1) * kPageRows > a.n) {
+      for (int e = 0; e < kPageRows; ++e) {
+        const int j = (page << kPageShift) + e;
+        win.xs[(q << kPageShift) + e] = j < a.n ? __ldg(static_cast<const X*>(a.x) + j) : X(0);
+      }
+    }
   }
+  bool timed_out = !mbar_wait(bar_setup, 0u);
   __syncthreads();
 
   // slot of row j in the window, or -1 (page outside the window)
   auto slot_of = [&](int j) -> int {
     const int t = (j >> kPageShift) - plo;
     if ((unsigned)t >= (unsigned)ntab) return -1;
-    const int q = tab[t];
-    return q < 0 ? -1 : ((q << kPageShift) | (j & (kPageRows - 1)));
+    const int base = tab[t];
+    return base < 0 ? -1 : base + (j & (kPageRows - 1));
   };
 
-  // ---- phase 2: stream the band's pairs
-  // Each thread takes 4 consecutive pairs per step (one 16-byte ja load, 16/8-byte value
-  // loads), and the loads of the next step are issued before the current step is
-  // processed. The row of a pair is searched between the rows that start the pair's
-  // 128-pair block and the next one (blk_row, precomputed), a few rows at most.
-  const int kbeg = __ldg(a.ia + r0);
-  const int kend = __ldg(a.ia + r1);
-  using XT = typename Acc<MODE>::X;
-  constexpr int kStep = 4 * kBandThreads;
-  int k0 = (kbeg & ~3) + 4 * tid;
-  int4 cj = make_int4(0, 0, 0, 0);
-  Raw4<MODE> cg{}, cv{};
-  if (k0 < kend) {
-    cj = ld_stream(reinterpret_cast<const int4*>(a.ja + k0));
-    cg = raw_load<MODE>(a.al, k0);
-    cv = raw_load<MODE>(a.au, k0);
-  }
-  for (; k0 < kend; k0 += kStep) {
-    const int kn = k0 + kStep;
-    int4 nj = make_int4(0, 0, 0, 0);
-    Raw4<MODE> ng{}, nv{};
-    if (kn < kend) {
-      nj = ld_stream(reinterpret_cast<const int4*>(a.ja + kn));
-      ng = raw_load<MODE>(a.al, kn);
-      nv = raw_load<MODE>(a.au, kn);
+  // ---- phase 2: stream the band's pairs, one row per group of G lanes. The rows of a
+  // stage are spread over the warps (group g of warp w takes row g * warps + w), so the
+  // lanes of one warp work on rows far apart and rarely hit the same window slot.
+  constexpr int W = T / 32, GPW = 32 / G;
+  const int rowoff = ((lane / G) % GPW) * W + warp;
+  const int gl = lane % G;  // lane within the group
+  // lanes of this group, for the shuffles that sum a row over the group
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  for (int s = 0; s < nstages && !timed_out; ++s) {
+    const int slot = s % NS;
+    const uint32_t parity = (uint32_t)((s / NS) & 1);
+    const int ks = s_sk[st0 + s];
+    const int ke = s_sk[st0 + s + 1];
+    const int r = s_sr[st0 + s] + rowoff;
+    int kb = 0, kx = 0;  // this group's pairs [kb, kx) of row r inside the stage
+    if (r < r1) {
+      kb = max(s_ia[r], ks);
+      kx = min(s_ia[r + 1], ke);
     }
-    const int jj[4] = {cj.x, cj.y, cj.z, cj.w};
-    // row of the first pair of this thread that lies inside the band
-    const int kf = k0 > kbeg ? k0 : kbeg;
-    const int blk = k0 >> kBlockShift;
-    int lo = max(__ldg(a.blk_row + blk), r0);
-    int hi = min(__ldg(a.blk_row + blk + 1), r1 - 1);
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (__ldg(a.ia + mid) <= kf) lo = mid; else hi = mid - 1;
+    if (!mbar_wait(bar_full + 8u * slot, parity)) {
+      timed_out = true;
+      break;
     }
-    int r = lo;
-    int rend = __ldg(a.ia + r + 1);
-    int rslot = slot_of(r);
-    if (rslot < 0) { bad |= 4u; rslot = 0; }
-    XT xr = win.xs[rslot];
-    Acc<MODE> acc;
-    acc.zero();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = k0 + q;
-      if (k < kbeg || k >= kend) continue;
-      while (k >= rend) {  // row change: hand the finished row segment to the window
-        if constexpr (MODE == MODE_DF) {
-          df_atomic_add(win.whi + rslot, win.wlo + rslot, acc.v);
-        } else {
-          atomicAdd(win.w + rslot, acc.v);
-        }
-        acc.zero();
-        ++r;
-        rend = __ldg(a.ia + r + 1);
-        rslot = slot_of(r);
-        if (rslot < 0) { bad |= 4u; rslot = 0; }
+    if (kb < kx) {  // the whole group enters (its lanes meet in the shuffles below)
+      const int base = ks & ~(kPairAlign - 1);
+      const int32_t* sja = ring_ja + (size_t)slot * SP - base;
+      const V* sal = ring_al + (size_t)slot * SP - base;
+      const V* sau = ring_au + (size_t)slot * SP - base;
+      int rslot = slot_of(r);
+      if (rslot < 0) {
+        bad |= 4u;
+        rslot = 0;
+      }
+      XR xr;
+      if constexpr (MODE == MODE_DF) {
+        xr = df_split<true>(win.xs[rslot], &bad);
+      } else {
         xr = win.xs[rslot];
       }
-      const int j = jj[q];
-      const int js = slot_of(j);
-      if constexpr (MODE == MODE_DF) {
-        df32 xj;
-        if (js >= 0) {
-          xj = win.xs[js];
-        } else {
-          xj = df_split<true>(__ldg(static_cast<const double*>(a.x) + j), &bad);
-        }
-        const df32 g = df_split<false>(raw_d(cg, q), nullptr);
-        const df32 sv = df_split<false>(raw_d(cv, q), nullptr);
-        df_acc_short(acc.v, df_mul(g, xj));
-        const df32 p = df_mul(sv, xr);
-        if (js >= 0) {
-          df_atomic_add(win.whi + js, win.wlo + js, p);
-        } else if (ATOMIC) {
-          atomicAdd(static_cast<double*>(a.y) + j, df_to_f64(p));
-        } else {
-          bad |= 4u;
-        }
-      } else if constexpr (MODE == MODE_F64) {
-        const double xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const double*>(a.x) + j);
-        acc.v = fma(raw_d(cg, q), xj, acc.v);
-        const double p = raw_d(cv, q) * xr;
-        if (js >= 0) {
-          atomicAdd(win.w + js, p);
-        } else if (ATOMIC) {
-          atomicAdd(static_cast<double*>(a.y) + j, p);
-        } else {
-          bad |= 4u;
+      X acc = X(0);
+      if constexpr (!ATOMIC) {
+        // Window strategy: the plan puts every target of the band in its window, so the
+        // slot lookup needs no branch (a page missing from the table would be a plan error:
+        // it is flagged, and its value goes to an in-range slot). U pairs per lane are
+        // loaded before any of them is scattered, so their shared-memory latencies overlap.
+        constexpr int U = 4;
+        for (int k0 = kb + gl; k0 < kx; k0 += U * G) {
+          int jv[U], sv[U];
+          V gv[U], vv[U];
+          X xv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            // past the row's end, re-read its first pair (an in-bounds address; the value is unused)
+            const int k = k0 + u * G < kx ? k0 + u * G : kb;
+            jv[u] = sja[k];
+            gv[u] = sal[k];
+            vv[u] = sau[k];
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int t = (jv[u] >> kPageShift) - plo;
+            const int pb = (unsigned)t < (unsigned)ntab ? tab[t] : -1;
+            bad |= pb < 0 ? 4u : 0u;
+            sv[u] = max(pb, 0) + (jv[u] & (kPageRows - 1));
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) xv[u] = win.xs[sv[u]];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (k0 + u * G < kx) {
+              if constexpr (MODE == MODE_DF) {
+                acc = fma(gv[u], xv[u], acc);
+                df_atomic_add(win.whi + sv[u], win.wlo + sv[u], df_mul(df_split<false>(vv[u], nullptr), xr));
+              } else if constexpr (MODE == MODE_F64) {
+                acc = fma(gv[u], xv[u], acc);
+                atomicAdd(win.w + sv[u], vv[u] * xr);
+              } else {
+                acc = __fmaf_rn(as_f32<MODE>(gv[u]), xv[u], acc);
+                atomicAdd(win.w + sv[u], __fmul_rn(as_f32<MODE>(vv[u]), xr));
+              }
+            }
+          }
         }
       } else {
-        const float xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const float*>(a.x) + j);
-        acc.v = __fmaf_rn(raw_f<MODE>(cg, q), xj, acc.v);
-        const float p = __fmul_rn(raw_f<MODE>(cv, q), xr);
-        if (js >= 0) {
-          atomicAdd(win.w + js, p);
-        } else if (ATOMIC) {
-          atomicAdd(static_cast<float*>(a.y) + j, p);
-        } else {
-          bad |= 4u;
+        // Atomic strategy: targets outside the window (plans with overflow) go to y in L2.
+        for (int k = kb + gl; k < kx; k += G) {
+          const int j = sja[k];
+          const int js = slot_of(j);
+          if constexpr (MODE == MODE_DF) {
+            const double xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const double*>(a.x) + j);
+            acc = fma(sal[k], xj, acc);
+            const df32 p = df_mul(df_split<false>(sau[k], nullptr), xr);
+            if (js >= 0) {
+              df_atomic_add(win.whi + js, win.wlo + js, p);
+            } else {
+              atomicAdd(static_cast<double*>(a.y) + j, (double)p.hi + (double)p.lo);
+            }
+          } else if constexpr (MODE == MODE_F64) {
+            const double xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const double*>(a.x) + j);
+            acc = fma(sal[k], xj, acc);
+            const double p = sau[k] * xr;
+            if (js >= 0) {
+              atomicAdd(win.w + js, p);
+            } else {
+              atomicAdd(static_cast<double*>(a.y) + j, p);
+            }
+          } else {
+            const float xj = js >= 0 ? win.xs[js] : __ldg(static_cast<const float*>(a.x) + j);
+            acc = __fmaf_rn(as_f32<MODE>(sal[k]), xj, acc);
+            const float p = __fmul_rn(as_f32<MODE>(sau[k]), xr);
+            if (js >= 0) {
+              atomicAdd(win.w + js, p);
+            } else {
+              atomicAdd(static_cast<float*>(a.y) + j, p);
+            }
+          }
         }
       }
+      // the group's gathered sum of row r: reduced across its G lanes, added once
+      if constexpr (MODE == MODE_DF) {
+        df32 t = df_split<false>(acc, nullptr);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          df32 u;
+          u.hi = __shfl_xor_sync(gmask, t.hi, o, G);
+          u.lo = __shfl_xor_sync(gmask, t.lo, o, G);
+          df_acc(t, u);
+        }
+        if (gl == 0) df_atomic_add(win.whi + rslot, win.wlo + rslot, t);
+      } else {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
+        if (gl == 0) atomicAdd(win.w + rslot, acc);
+      }
     }
-    if constexpr (MODE == MODE_DF) {
-      df_atomic_add(win.whi + rslot, win.wlo + rslot, acc.v);
-    } else {
-      atomicAdd(win.w + rslot, acc.v);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar_empty + 8u * slot);
+    if (tid == 0 && issued < nstages) {
+      // every warp is done with stage s: refill its ring slot with stage s + NS
+      if (!mbar_wait(bar_empty + 8u * slot, parity)) {
+        timed_out = true;
+        break;
+      }
+      fence_proxy_async_smem();
+      issue(issued, s_sk[st0 + issued], s_sk[st0 + issued + 1]);
+      ++issued;
     }
-    cj = nj;
-    cg = ng;
-    cv = nv;
   }
-  __syncthreads();
 
-  // ---- phase 3: own rows (diagonal term added here, so empty rows are covered)
-  for (int r = r0 + tid; r < r1; r += kBandThreads) {
-    int s = slot_of(r);
-    if (s < 0) { bad |= 4u; continue; }
-    if constexpr (MODE == MODE_DF) {
-      df32 v;
-      v.hi = win.whi[s];
-      v.lo = win.wlo[s];
-      const df32 dd = df_split<false>(__ldg(static_cast<const double*>(a.ad) + r), nullptr);
-      df_acc(v, df_mul(dd, win.xs[s]));
-      const double out = df_to_f64(v);
-      if (ATOMIC) atomicAdd(static_cast<double*>(a.y) + r, out);
-      else static_cast<double*>(a.y)[r] = out;
-    } else if constexpr (MODE == MODE_F64) {
-      const double out = fma(__ldg(static_cast<const double*>(a.ad) + r), win.xs[s], win.w[s]);
+  // ---- a wait ran out (should not happen): let this thread's copies land, then stop
+  __shared__ int abort_flag;
+  if (tid == 0) abort_flag = 0;
+  __syncthreads();
+  if (timed_out) abort_flag = 1;
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) {
+      mbar_wait(bar_setup, 0u);
+      for (int s = 0; s < issued; ++s) mbar_wait(bar_full + 8u * (s % NS), (uint32_t)((s / NS) & 1));
+      atomicOr(a.status, DEV_TIMEOUT);
+    }
+    return;
+  }
+
+  // ---- phase 3: own rows (the diagonal term is added here, so rows without pairs are covered)
+  for (int r = r0 + tid; r < r1; r += T) {
+    const int s = slot_of(r);
+    if (s < 0) {
+      bad |= 4u;
+      continue;
+    }
+    if constexpr (MODE == MODE_DF || MODE == MODE_F64) {
+      const double out = fma(__ldg(static_cast<const double*>(a.ad) + r), win.xs[s], win.value(s));
       if (ATOMIC) atomicAdd(static_cast<double*>(a.y) + r, out);
       else static_cast<double*>(a.y)[r] = out;
     } else {
-      const float out = __fmaf_rn(load_one_f<MODE>(a.ad, r), win.xs[s], win.w[s]);
+      const float out =
+          __fmaf_rn(as_f32<MODE>(__ldg(static_cast<const V*>(a.ad) + r)), win.xs[s], win.value(s));
       if (ATOMIC) atomicAdd(static_cast<float*>(a.y) + r, out);
       else static_cast<float*>(a.y)[r] = out;
     }
   }
 
   // ---- phase 4: rows below r0 (one warp per window page)
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  for (int q = warp; q < np; q += kBandThreads / 32) {
+  for (int q = warp; q < np; q += T / 32) {
     const uint64_t mask = __ldg(reinterpret_cast<const unsigned long long*>(a.wmask) + wp0 + q);
     if (mask == 0ull) continue;
     const int base = __ldg(a.wbase + wp0 + q);
@@ -361,20 +518,9 @@ __global__ void __launch_bounds__(kBandThreads, 2) band_kernel(BandArgs a) {
       const int s = (q << kPageShift) | e;
       const int row = (page << kPageShift) | e;
       const int pos = base + __popcll(mask & ((1ull << e) - 1ull));
-      if constexpr (MODE == MODE_DF) {
-        df32 v;
-        v.hi = win.whi[s];
-        v.lo = win.wlo[s];
-        const double out = df_to_f64(v);
-        if (ATOMIC) atomicAdd(static_cast<double*>(a.y) + row, out);
-        else static_cast<double*>(a.spill)[pos] = out;
-      } else if constexpr (MODE == MODE_F64) {
-        if (ATOMIC) atomicAdd(static_cast<double*>(a.y) + row, win.w[s]);
-        else static_cast<double*>(a.spill)[pos] = win.w[s];
-      } else {
-        if (ATOMIC) atomicAdd(static_cast<float*>(a.y) + row, win.w[s]);
-        else static_cast<float*>(a.spill)[pos] = win.w[s];
-      }
+      const X v = win.value(s);
+      if (ATOMIC) atomicAdd(static_cast<X*>(a.y) + row, v);
+      else static_cast<X*>(a.spill)[pos] = v;
     }
   }
   if (bad) atomicOr(a.status, (int)((bad & 1u) ? DEV_RANGE : 0) | (int)((bad & 4u) ? DEV_BOUNDS : 0));
@@ -396,42 +542,61 @@ __global__ void accumulate_kernel(int64_t nacc, const int32_t* __restrict__ acc_
 }
 
 // ---------------------------------------------------------------------------- launchers
-static int mode_of(Arith arith, int storage) {
-  if (storage == CSRC_F32) return MODE_F32;
-  if (storage == CSRC_BF16) return MODE_BF16;
-  return arith == ARITH_F64 ? MODE_F64 : MODE_DF;
+template <int MODE, int G, bool ATOMIC>
+static cudaError_t set_smem_one() {
+  return cudaFuncSetAttribute(band_kernel<MODE, G, ATOMIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              band_smem_limit(MODE));
 }
 
-template <int MODE, bool ATOMIC>
-static cudaError_t set_smem(int bytes) {
-  return cudaFuncSetAttribute(band_kernel<MODE, ATOMIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-cudaError_t prepare_band_kernels(int max_smem_bytes) {
-  cudaError_t e = cudaSuccess;
-  cudaError_t r;
-#define CSRC_SET(M, A) r = set_smem<M, A>(max_smem_bytes); if (r != cudaSuccess) e = r;
-  CSRC_SET(MODE_DF, false) CSRC_SET(MODE_DF, true) CSRC_SET(MODE_F64, false) CSRC_SET(MODE_F64, true)
-  CSRC_SET(MODE_F32, false) CSRC_SET(MODE_F32, true) CSRC_SET(MODE_BF16, false) CSRC_SET(MODE_BF16, true)
-#undef CSRC_SET
+template <int MODE>
+static cudaError_t set_smem_mode() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = set_smem_one<MODE, 1, false>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 1, true>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 2, false>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 2, true>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 4, false>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 4, true>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 8, false>()) != cudaSuccess) e = r;
+  if ((r = set_smem_one<MODE, 8, true>()) != cudaSuccess) e = r;
   return e;
+}
+
+cudaError_t prepare_band_kernels() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = set_smem_mode<MODE_DF>()) != cudaSuccess) e = r;
+  if ((r = set_smem_mode<MODE_F64>()) != cudaSuccess) e = r;
+  if ((r = set_smem_mode<MODE_F32>()) != cudaSuccess) e = r;
+  if ((r = set_smem_mode<MODE_BF16>()) != cudaSuccess) e = r;
+  return e;
+}
+
+template <int MODE>
+static void launch_mode(int group, bool atomic, const BandArgs& a, dim3 grid, int smem, cudaStream_t s) {
+  constexpr int T = BandShape<MODE>::T;
+#define CSRC_G(GV)                                                           \
+  if (atomic) band_kernel<MODE, GV, true><<<grid, T, smem, s>>>(a);          \
+  else band_kernel<MODE, GV, false><<<grid, T, smem, s>>>(a);
+  switch (group) {
+    case 1: CSRC_G(1) break;
+    case 2: CSRC_G(2) break;
+    case 4: CSRC_G(4) break;
+    default: CSRC_G(8) break;
+  }
+#undef CSRC_G
 }
 
 cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandArgs& a, int nbands, int smem,
                         cudaStream_t s) {
   if (nbands <= 0) return cudaSuccess;
   const int mode = mode_of(arith, storage);
-  dim3 grid(nbands), block(kBandThreads);
-#define CSRC_LAUNCH(M)                                                        \
-  if (atomic_flush) band_kernel<M, true><<<grid, block, smem, s>>>(a);        \
-  else band_kernel<M, false><<<grid, block, smem, s>>>(a);
+  dim3 grid(nbands);
   switch (mode) {
-    case MODE_DF: CSRC_LAUNCH(MODE_DF) break;
-    case MODE_F64: CSRC_LAUNCH(MODE_F64) break;
-    case MODE_F32: CSRC_LAUNCH(MODE_F32) break;
-    default: CSRC_LAUNCH(MODE_BF16) break;
+    case MODE_DF: launch_mode<MODE_DF>(a.group, atomic_flush, a, grid, smem, s); break;
+    case MODE_F64: launch_mode<MODE_F64>(a.group, atomic_flush, a, grid, smem, s); break;
+    case MODE_F32: launch_mode<MODE_F32>(a.group, atomic_flush, a, grid, smem, s); break;
+    default: launch_mode<MODE_BF16>(a.group, atomic_flush, a, grid, smem, s); break;
   }
-#undef CSRC_LAUNCH
   return cudaGetLastError();
 }
 
