@@ -38,6 +38,11 @@ struct csrc_matrix_s {
   DevPlan plan;
   bool have_plan = false;
   bool plan_covers = false;   // every scatter target lies in its band's window
+  int32_t part_nbands = 0;    // band count requested for the partition (0 = automatic)
+  // plans for several right-hand sides: RK = 2, 4, 8 columns per pass (windows RK times wider)
+  DevPlan plan_rk[3];
+  bool have_rk[3] = {false, false, false};
+  bool covers_rk[3] = {false, false, false};
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -46,6 +51,7 @@ struct csrc_matrix_s {
   void* d_xs = nullptr;
   void* d_ys = nullptr;
   int32_t tuned = 0;
+  int32_t tuned_rk = 0;       // columns per pass for several right-hand sides (0 = up to 8)
   // kernel timing (csrc_set_profiling): CUDA events around every launch of this handle
   bool profiling = false;
   struct TimedLaunch {
@@ -204,7 +210,7 @@ int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int
 // out by BandLayout) fits `budget` bytes. A band that does not fit is split at its
 // non-zero midpoint. A single row that still does not fit gets a capped window when
 // allow_overflow (targets outside it take the global-atomic path); otherwise planning fails.
-bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int mode,
+bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int mode, int rk,
                      bool allow_overflow, int32_t stage_rows, int32_t stage_cap, HostPlan& hp) {
   const int32_t n = h->n;
   const std::vector<int32_t>& ia = h->ia;
@@ -213,7 +219,7 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
   std::vector<int32_t> page_stamp((size_t)npages + 1, -1), row_stamp((size_t)n + 1, -1);
   int32_t stamp = 0;
   std::vector<int32_t> pages;
-  const int xb = window_x_bytes(mode), ab = window_acc_bytes(mode);
+  const int xb = rk * window_x_bytes(mode), ab = rk * window_acc_bytes(mode);
   auto bytes_of = [&](int64_t np, int64_t ntab, int32_t r0, int32_t r1, int32_t nst) -> int64_t {
     if (np > 32767 || ntab > (1 << 24)) return INT64_MAX;
     const int32_t st0 = (int32_t)hp.stage_k.size();
@@ -315,7 +321,10 @@ cudaError_t upload(T** d, const std::vector<T>& v, cudaStream_t s) {
   return e;
 }
 
-csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
+// Window plan for rk columns per pass into p (freed first). Sets covers when every
+// scatter target of every band lies in its window.
+csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, DevPlan& p, bool& covers,
+                       std::vector<int32_t>* part_out) {
   // paper-rule partition
   int32_t nb = nbands;
   if (nb <= 0) {
@@ -334,12 +343,12 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   int32_t group = 1;
   while (group < 8 && (double)(kBandThreads / group) * avg > (double)kStageCap) group *= 2;
   HostPlan hp;
-  bool ok = build_host_plan(h, part, budget, mode, false, kBandThreads / group, kStageCap, hp);
-  if (!ok) {
+  bool ok = build_host_plan(h, part, budget, mode, rk, false, kBandThreads / group, kStageCap, hp);
+  if (!ok && rk == 1) {
     hp = HostPlan();
-    ok = build_host_plan(h, part, budget, mode, true, kBandThreads / group, kStageCap, hp);
-    if (!ok) return CSRC_ERR_NOT_PARTITIONED;
+    ok = build_host_plan(h, part, budget, mode, rk, true, kBandThreads / group, kStageCap, hp);
   }
+  if (!ok) return CSRC_ERR_NOT_PARTITIONED;
   // accumulation map: group spill entries by row (stable: band order)
   std::vector<int32_t> cnt((size_t)h->n + 1, 0);
   for (size_t q = 0; q < hp.wpage.size(); ++q) {
@@ -371,8 +380,7 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
     }
   }
   // upload
-  free_plan(h->plan);
-  DevPlan& p = h->plan;
+  free_plan(p);
   cudaStream_t s = 0;
   p.nb = (int32_t)hp.band_row.size() - 1;
   if (h->n == 0) p.nb = 0;
@@ -391,7 +399,7 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   CSRC_TRY(upload(&p.band_stage, hp.band_stage, s));
   CSRC_TRY(upload(&p.stage_k, hp.stage_k, s));
   CSRC_TRY(upload(&p.stage_r, hp.stage_r, s));
-  CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * h->xbytes())));
+  CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * rk * h->xbytes())));
   CSRC_TRY(cudaStreamSynchronize(s));
   p.spill = hp.spill;
   p.group = group;
@@ -401,9 +409,40 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   p.max_tab = hp.max_tab;
   p.smem_bytes = band_ring_bytes(mode) + hp.smem;
   p.total_pages = (int64_t)hp.wpage.size();
-  h->part = part;
+  covers = hp.covers;
+  if (part_out) part_out->swap(part);
+  return CSRC_OK;
+}
+
+// The single-vector plan (and the partition it comes from); plans for several
+// right-hand sides are rebuilt from the same band count when next needed.
+csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
+  for (int i = 0; i < 3; ++i) {
+    free_plan(h->plan_rk[i]);
+    h->have_rk[i] = false;
+  }
+  h->have_plan = false;
+  CSRC_TRY_S(build_plan(h, nbands, 1, h->plan, h->plan_covers, &h->part));
+  h->part_nbands = nbands;
   h->have_plan = true;
-  h->plan_covers = hp.covers;
+  return CSRC_OK;
+}
+
+// The plan for rk columns per pass (rk = 1, 2, 4 or 8), built on first use.
+csrc_status plan_for(csrc_matrix_s* h, int rk, DevPlan** out, bool* covers) {
+  if (rk == 1) {
+    if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
+    *out = &h->plan;
+    *covers = h->plan_covers;
+    return CSRC_OK;
+  }
+  const int i = rk == 2 ? 0 : (rk == 4 ? 1 : 2);
+  if (!h->have_rk[i]) {
+    CSRC_TRY_S(build_plan(h, h->part_nbands, rk, h->plan_rk[i], h->covers_rk[i], nullptr));
+    h->have_rk[i] = true;
+  }
+  *out = &h->plan_rk[i];
+  *covers = h->covers_rk[i];
   return CSRC_OK;
 }
 
@@ -459,33 +498,37 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Arguments of one band-kernel launch: the handle's arrays and plan, al and au swapped
-// for the transpose (Section 5).
-BandArgs band_args(const csrc_matrix_s* h, bool transpose, const void* x, void* y, void* spill) {
+// Arguments of one band-kernel launch: the handle's arrays and plan p, al and au swapped
+// for the transpose (Section 5); x and y point at the pass's first column, ldx is their
+// row stride and rk the columns per pass.
+BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, const void* x, void* y, void* spill,
+                   int ldx, int rk) {
   BandArgs a;
   a.n = h->n;
   a.ia = h->d_ia;
   a.ja = h->d_ja;
-  a.band_stage = h->plan.band_stage;
-  a.stage_k = h->plan.stage_k;
-  a.stage_r = h->plan.stage_r;
-  a.group = h->plan.group;
+  a.band_stage = p.band_stage;
+  a.stage_k = p.stage_k;
+  a.stage_r = p.stage_r;
+  a.group = p.group;
   a.al = transpose ? h->d_au : h->d_al;  // gathered values
   a.au = transpose ? h->d_al : h->d_au;  // scattered values
   a.ad = h->d_ad;
   a.x = x;
   a.y = y;
-  a.band_row = h->plan.band_row;
-  a.band_plo = h->plan.band_plo;
-  a.band_ntab = h->plan.band_ntab;
-  a.band_wp = h->plan.band_wp;
-  a.wpage = h->plan.wpage;
-  a.wbase = h->plan.wbase;
-  a.wmask = h->plan.wmask;
+  a.band_row = p.band_row;
+  a.band_plo = p.band_plo;
+  a.band_ntab = p.band_ntab;
+  a.band_wp = p.band_wp;
+  a.wpage = p.wpage;
+  a.wbase = p.wbase;
+  a.wmask = p.wmask;
   a.spill = spill;
   a.status = h->d_status;
   a.band_offset = 0;
   a.x_bulk = (reinterpret_cast<uintptr_t>(x) & 15u) == 0u;
+  a.ldx = ldx;
+  a.rk = rk;
   return a;
 }
 
@@ -531,18 +574,52 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
       }));
     }
   } else {
-    const BandArgs a = band_args(h, transpose, dx, dy, h->plan.spill_buf);
+    const BandArgs a = band_args(h, h->plan, transpose, dx, dy, h->plan.spill_buf, 1, 1);
     const bool atomic = strat == CSRC_STRAT_ATOMIC;
     if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
                           [&] { return launch_band(h->arith, h->storage, atomic, a, h->plan.nb, h->plan.smem_bytes, s); }));
     if (!atomic && h->plan.nacc > 0)
       CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
-        return launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
+        return launch_accumulate(h->arith, h->storage, h->plan.nacc, 1, 1, h->plan.acc_row, h->plan.acc_ptr,
                                  h->plan.acc_src, h->plan.spill_buf, dy, s);
       }));
   }
   if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, s));
+  return CSRC_OK;
+}
+
+// Y = A X (or A^T X) for one handle, X and Y n-by-nrhs row-major device blocks: the
+// columns are cut into passes of rk = 8, 4, 2 or 1 columns (the handle's tuned k-tile caps
+// rk), and each pass runs the band kernel and the accumulation kernel on its columns.
+csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, bool transpose, cudaStream_t s) {
+  if (h->n == 0) return CSRC_OK;
+  const size_t vb = (size_t)h->n * (size_t)nrhs * h->xbytes();
+  const char* xa = static_cast<const char*>(X);
+  const char* ya = static_cast<const char*>(Y);
+  if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
+  if (!is_device_ptr(X) || !is_device_ptr(Y)) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  const int cap = h->tuned_rk > 0 ? h->tuned_rk : 8;
+  for (int32_t c0 = 0; c0 < nrhs;) {
+    int rk = 8;
+    while (rk > 1 && (rk > cap || c0 + rk > nrhs)) rk /= 2;
+    DevPlan* p = nullptr;
+    bool covers = false;
+    CSRC_TRY_S(plan_for(h, rk, &p, &covers));
+    if (!covers) return CSRC_ERR_NOT_PARTITIONED;
+    const void* xc = static_cast<const char*>(X) + (size_t)c0 * h->xbytes();
+    void* yc = static_cast<char*>(Y) + (size_t)c0 * h->xbytes();
+    const BandArgs a = band_args(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk);
+    CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
+                          [&] { return launch_band(h->arith, h->storage, false, a, p->nb, p->smem_bytes, s); }));
+    if (p->nacc > 0)
+      CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
+        return launch_accumulate(h->arith, h->storage, p->nacc, rk, nrhs, p->acc_row, p->acc_ptr, p->acc_src,
+                                 p->spill_buf, yc, s);
+      }));
+    c0 += rk;
+  }
   return CSRC_OK;
 }
 
@@ -724,10 +801,10 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   if (!h->have_plan || !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
   if (h->plan.spill > capacity) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
-  const BandArgs a = band_args(h, transpose, x, y, spill);
+  const BandArgs a = band_args(h, h->plan, transpose, x, y, spill, 1, 1);
   CSRC_TRY(launch_band(h->arith, h->storage, false, a, h->plan.nb, h->plan.smem_bytes, s));
   if (h->plan.nacc > 0)
-    CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, h->plan.acc_row, h->plan.acc_ptr,
+    CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, 1, 1, h->plan.acc_row, h->plan.acc_ptr,
                                h->plan.acc_src, spill, y, s));
   return CSRC_OK;
 }
@@ -915,15 +992,14 @@ csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy str
 csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
                               int32_t nrhs, int32_t transpose, cudaStream_t stream) {
   if (batch < 0 || nrhs <= 0 || (batch > 0 && (!hs || !X || !Y))) return CSRC_ERR_INVALID_ARG;
-  if (nrhs != 1) return CSRC_ERR_INVALID_ARG;
   for (int32_t b = 0; b < batch; ++b) {
-    if (!hs[b]) return CSRC_ERR_INVALID_ARG;
+    if (!hs[b] || !X[b] || !Y[b]) return CSRC_ERR_INVALID_ARG;
     if (hs[b]->storage != hs[0]->storage) return CSRC_ERR_MISMATCH;
   }
-  for (int32_t b = 0; b < batch; ++b) {
-    csrc_status st = transpose ? csrc_spmv_t(hs[b], X[b], Y[b], CSRC_STRAT_AUTO, stream)
-                               : csrc_spmv(hs[b], X[b], Y[b], CSRC_STRAT_AUTO, stream);
-    if (st != CSRC_OK) return st;
+  try {
+    for (int32_t b = 0; b < batch; ++b) CSRC_TRY_S(spmm_one(hs[b], X[b], Y[b], nrhs, transpose != 0, stream));
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
   }
   return CSRC_OK;
 }
@@ -1007,6 +1083,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   ensure_device(h);
   cudaDeviceSynchronize();
   free_plan(h->plan);
+  for (int i = 0; i < 3; ++i) free_plan(h->plan_rk[i]);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);

@@ -147,6 +147,8 @@ struct BandArgs {
   const int32_t* stage_r;
   int32_t group;  // lanes per row
   int32_t x_bulk; // x is 16-byte aligned: window pages of x are fetched with bulk copies
+  int32_t ldx;    // row stride of x and y in elements (1 for a single vector)
+  int32_t rk;     // columns per pass (1, 2, 4 or 8); x and y point at the pass's first column
   const void* al;  // gathered values  (au for the transpose)
   const void* au;  // scattered values (al for the transpose)
   const void* ad;
@@ -170,10 +172,12 @@ enum : int32_t { DEV_RANGE = 1, DEV_TIMEOUT = 2, DEV_BOUNDS = 4 };
 // Launchers (kernels.cu). All return cudaGetLastError() of their launch.
 cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandArgs& a, int nbands,
                         int smem_bytes, cudaStream_t s);
-cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, const int32_t* acc_row,
+cudaError_t launch_band_rk(Arith arith, int storage, const BandArgs& a, int nbands, int smem, cudaStream_t s);
+cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, int ldx, const int32_t* acc_row,
                               const int32_t* acc_ptr, const int32_t* acc_src, const void* spill, void* y,
                               cudaStream_t s);
 cudaError_t prepare_band_kernels();
+cudaError_t prepare_band_kernels_rk();
 
 // Product into caller-provided spill memory, allocating nothing (api.cpp; used by noalloc.cu).
 int32_t handle_device(const csrc_matrix_s* h);

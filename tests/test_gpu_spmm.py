@@ -1,0 +1,116 @@
+"""GPU parity of the several-right-hand-side product Y = A X (and A^T X), X n-by-r row-major.
+
+The oracle applies Fig. 2(a) to each column. Tolerances per row and column are those of
+the single-vector product: 1e-12 (FP64 storage), 1e-5 (FP32), 1e-2 (BF16), relative to
+sum_j |a_ij||x_jc|. Integer-valued inputs are exact in every storage type, so there the
+results must match bit for bit.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fe_inputs as fe
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def cs():
+    from paper_1003_0952_gb300 import build
+
+    build.build()
+    import paper_1003_0952_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return m
+
+
+def _transpose(m):
+    at = sp.csr_matrix((m.val, m.col, m.row_ptr), shape=(m.n, m.n)).T.tocsr()
+    return fe.FEMatrix(m.n, at.indptr.astype(np.int64), at.indices.astype(np.int32), at.data)
+
+
+def _run(cs, h, X, storage, transpose):
+    dt = torch.float64 if storage == "f64" else torch.float32
+    Xd = torch.as_tensor(X, dtype=dt).cuda().contiguous()
+    Yd = torch.full_like(Xd, float("nan"))
+    cs.csrc_spmm_batched([h], [Xd], [Yd], X.shape[1], transpose, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    st = cs.csrc_get_last_device_error(h)
+    assert st == cs.CSRC_OK, cs.csrc_status_string(st)
+    return Yd.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 8, 13, 32])
+def test_spmm_matches_oracle(cs, storage, nrhs):
+    m = fe.q1_hex(12, 1, 31)  # scalar Q1, RCM order, n = 1728
+    c = oracle.from_matrix(m)
+    X = fe.source_vector(m.n, 41, nrhs=nrhs)
+    if storage != "f64":
+        X = X.astype(np.float32).astype(np.float64)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+    try:
+        cs.csrc_partition(h, 0)
+        for tr in (False, True):
+            Y = _run(cs, h, X, storage, tr)
+            Yref = oracle.csrc_spmm(c, X, transpose=tr)
+            mm = _transpose(m) if tr else m
+            err = oracle.max_rel_err(mm, X, Y, Yref)
+            assert err <= TOL[storage], (tr, err)
+    finally:
+        cs.csrc_destroy(h)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_spmm_integer_values_bit_exact(cs, storage):
+    for m in (fe.q1_hex(7, 3, 5), fe.p1_grid(23, 17, 6), fe.tet_mesh(2000, 7, method="kuhn")):
+        im = fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 77))
+        c = oracle.from_matrix(im)
+        X = fe.integer_vector(m.n, 78, nrhs=6)
+        h = cs.csrc_create_from_csr(im.n, im.row_ptr, im.col, im.val, cs.STORAGE[storage])
+        try:
+            cs.csrc_partition(h, 7)
+            for tr in (False, True):
+                np.testing.assert_array_equal(_run(cs, h, X, storage, tr), oracle.csrc_spmm(c, X, transpose=tr))
+        finally:
+            cs.csrc_destroy(h)
+
+
+def test_spmm_columns_equal_single_vector_products(cs):
+    # a one-column block is the single-vector product, and every column of a block is one
+    m = fe.q1_hex(10, 3, 8)
+    X = fe.source_vector(m.n, 9, nrhs=4)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        Y = _run(cs, h, X, "f64", False)
+        for col in range(4):
+            xd = torch.from_numpy(np.ascontiguousarray(X[:, col])).cuda()
+            yd = torch.empty_like(xd)
+            cs.csrc_spmv(h, xd, yd, cs.CSRC_STRAT_WINDOW)
+            torch.cuda.synchronize()
+            assert oracle.max_rel_err(m, X[:, col], Y[:, col], yd.cpu().numpy()) <= 1e-12
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_spmm_batch_of_uneven_members(cs):
+    ms = [fe.p1_grid(9, 7, 1), fe.q1_hex(6, 3, 2), fe.tet_mesh(900, 3, method="kuhn"), fe.p1_grid(40, 3, 4)]
+    hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64) for m in ms]
+    try:
+        Xs = [fe.source_vector(m.n, 10 + i, nrhs=5) for i, m in enumerate(ms)]
+        Xd = [torch.from_numpy(x).cuda() for x in Xs]
+        Yd = [torch.full_like(x, float("nan")) for x in Xd]
+        cs.csrc_spmm_batched(hs, Xd, Yd, 5, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for m, X, Y in zip(ms, Xs, Yd):
+            err = oracle.max_rel_err(m, X, Y.cpu().numpy(), oracle.csrc_spmm(oracle.from_matrix(m), X))
+            assert err <= 1e-12
+    finally:
+        for h in hs:
+            cs.csrc_destroy(h)
