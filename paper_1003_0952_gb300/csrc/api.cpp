@@ -52,10 +52,12 @@ struct csrc_matrix_s {
   void* d_ys = nullptr;
   int32_t tuned = 0;
   int32_t tuned_rk = 0;       // columns per pass for several right-hand sides (0 = up to 8)
+  uint64_t generation = 0;    // bumped whenever plans or the tuned strategy change
   // kernel timing (csrc_set_profiling): CUDA events around every launch of this handle
   bool profiling = false;
   struct TimedLaunch {
     int32_t kind;
+    int32_t kernels;  // kernel launches the record covers (a graph replay covers several)
     cudaEvent_t start, stop;
   };
   std::vector<TimedLaunch> timed;
@@ -409,6 +411,9 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, DevPlan& p, boo
   p.max_tab = hp.max_tab;
   p.smem_bytes = band_ring_bytes(mode) + hp.smem;
   p.total_pages = (int64_t)hp.wpage.size();
+  p.band_pairs.resize((size_t)p.nb);
+  for (int32_t b = 0; b < p.nb; ++b)
+    p.band_pairs[(size_t)b] = (int64_t)h->ia[(size_t)hp.band_row[(size_t)b + 1]] - h->ia[(size_t)hp.band_row[(size_t)b]];
   covers = hp.covers;
   if (part_out) part_out->swap(part);
   return CSRC_OK;
@@ -425,6 +430,7 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
   CSRC_TRY_S(build_plan(h, nbands, 1, h->plan, h->plan_covers, &h->part));
   h->part_nbands = nbands;
   h->have_plan = true;
+  ++h->generation;
   return CSRC_OK;
 }
 
@@ -462,7 +468,7 @@ cudaEvent_t pooled_event(csrc_matrix_s* h) {
 
 // Runs `launch` on stream s; with profiling on, brackets it with a pair of events.
 template <typename F>
-cudaError_t timed_launch(csrc_matrix_s* h, int32_t kind, cudaStream_t s, F&& launch) {
+cudaError_t timed_launch(csrc_matrix_s* h, int32_t kind, cudaStream_t s, F&& launch, int32_t kernels = 1) {
   if (!h->profiling) return launch();
   cudaEvent_t a = pooled_event(h), b = pooled_event(h);
   if (!a || !b) return cudaErrorMemoryAllocation;
@@ -470,7 +476,7 @@ cudaError_t timed_launch(csrc_matrix_s* h, int32_t kind, cudaStream_t s, F&& lau
   if (e == cudaSuccess) e = launch();
   if (e == cudaSuccess) e = cudaEventRecord(b, s);
   if (e != cudaSuccess) return e;
-  h->timed.push_back({kind, a, b});
+  h->timed.push_back({kind, kernels, a, b});
   return cudaSuccess;
 }
 
@@ -623,6 +629,196 @@ csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, boo
   return CSRC_OK;
 }
 
+// ---------------------------------------------------------------------------- batched products
+// A batch executor: the (member, band) tiles of a batch of single-vector products, the
+// members' kernel arguments on the device, and the CUDA graph that runs them (memsets of
+// the atomic members' y, one persistent band kernel per (G, strategy) group, one
+// accumulation kernel for every window member). Executors are cached by their arguments
+// and replayed while the members' plans are unchanged.
+struct BatchExec {
+  int device = 0;
+  std::vector<csrc_matrix_s*> hs;
+  std::vector<uint64_t> gens;
+  std::vector<const void*> xs;
+  std::vector<void*> ys;
+  int transpose = 0;
+  BandArgs* d_members = nullptr;
+  int2* d_tiles = nullptr;
+  int* d_counters = nullptr;
+  AccArgs* d_acc = nullptr;
+  int64_t* d_offs = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;  // kernel launches per replay
+  ~BatchExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    dfree(d_members); dfree(d_tiles); dfree(d_counters); dfree(d_acc); dfree(d_offs);
+  }
+};
+
+std::mutex g_batch_mutex;
+std::vector<BatchExec*> g_batches;  // most recently used last
+constexpr size_t kMaxBatches = 8;
+
+void drop_batches_of(const csrc_matrix_s* h) {
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  for (size_t i = 0; i < g_batches.size();) {
+    BatchExec* e = g_batches[i];
+    if (std::find(e->hs.begin(), e->hs.end(), h) != e->hs.end()) {
+      delete e;
+      g_batches.erase(g_batches.begin() + (long)i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+bool batch_matches(const BatchExec* e, const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
+                   int transpose, int device) {
+  if (e->device != device || e->transpose != transpose || (int32_t)e->hs.size() != batch) return false;
+  for (int32_t b = 0; b < batch; ++b)
+    if (e->hs[(size_t)b] != hs[b] || e->gens[(size_t)b] != hs[b]->generation || e->xs[(size_t)b] != X[b] ||
+        e->ys[(size_t)b] != Y[b])
+      return false;
+  return true;
+}
+
+csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int transpose,
+                        int device, BatchExec** out) {
+  BatchExec* e = new BatchExec();
+  auto fail = [&](csrc_status st) {
+    delete e;
+    return st;
+  };
+  e->device = device;
+  e->transpose = transpose;
+  int sms = 1;
+  std::vector<BandArgs> members((size_t)batch);
+  std::vector<AccArgs> accs;
+  std::vector<int64_t> offs{0};
+  struct Tile { int32_t member, band; int64_t pairs; };
+  std::vector<Tile> groups[4][2];  // [log2 G][atomic]
+  std::vector<std::pair<void*, size_t>> zero_y;
+  int smem = 0;
+  for (int32_t b = 0; b < batch; ++b) {
+    csrc_matrix_s* h = hs[b];
+    sms = std::max(sms, h->sms);
+    e->hs.push_back(h);
+    e->xs.push_back(X[b]);
+    e->ys.push_back(Y[b]);
+    if (h->n == 0) {
+      e->gens.push_back(h->generation);
+      continue;
+    }
+    if (!is_device_ptr(X[b]) || !is_device_ptr(Y[b])) return fail(CSRC_ERR_INVALID_ARG);
+    const size_t vb = (size_t)h->n * h->xbytes();
+    const char* xa = static_cast<const char*>(X[b]);
+    const char* ya = static_cast<const char*>(Y[b]);
+    if (xa < ya + vb && ya < xa + vb) return fail(CSRC_ERR_ALIAS);
+    DevPlan* p = nullptr;
+    bool covers = false;
+    csrc_status st = plan_for(h, 1, &p, &covers);
+    if (st != CSRC_OK) return fail(st);
+    e->gens.push_back(h->generation);
+    const bool atomic = h->tuned == CSRC_STRAT_ATOMIC || !covers;
+    members[(size_t)b] = band_args(h, *p, transpose != 0, X[b], Y[b], p->spill_buf, 1, 1);
+    const int lg = p->group == 1 ? 0 : (p->group == 2 ? 1 : (p->group == 4 ? 2 : 3));
+    for (int32_t band = 0; band < p->nb; ++band)
+      groups[lg][atomic ? 1 : 0].push_back({b, band, p->band_pairs[(size_t)band]});
+    smem = std::max(smem, p->smem_bytes);
+    if (atomic) {
+      zero_y.push_back({Y[b], vb});
+    } else if (p->nacc > 0) {
+      accs.push_back({p->acc_row, p->acc_ptr, p->acc_src, p->spill_buf, Y[b]});
+      offs.push_back(offs.back() + p->nacc);
+    }
+  }
+  // tiles, largest bands first within each group
+  std::vector<int2> tiles;
+  struct Launch { int group; bool atomic; int first, count; };
+  std::vector<Launch> launches;
+  for (int lg = 0; lg < 4; ++lg)
+    for (int at = 0; at < 2; ++at) {
+      auto& v = groups[lg][at];
+      if (v.empty()) continue;
+      std::stable_sort(v.begin(), v.end(), [](const Tile& a, const Tile& b) { return a.pairs > b.pairs; });
+      launches.push_back({1 << lg, at != 0, (int)tiles.size(), (int)v.size()});
+      for (const Tile& t : v) {
+        int2 mt;
+        mt.x = t.member;
+        mt.y = t.band;
+        tiles.push_back(mt);
+      }
+    }
+  cudaStream_t s = nullptr;
+  cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return fail(from_cuda(ce));
+  auto done = [&](cudaError_t err) -> csrc_status {
+    if (s) cudaStreamDestroy(s);
+    if (err != cudaSuccess) return fail(from_cuda(err));
+    return CSRC_OK;
+  };
+  if ((ce = upload(&e->d_members, members, s)) != cudaSuccess) return done(ce);
+  if ((ce = upload(&e->d_tiles, tiles, s)) != cudaSuccess) return done(ce);
+  if ((ce = dmalloc(&e->d_counters, std::max<size_t>(1, launches.size()))) != cudaSuccess) return done(ce);
+  if ((ce = upload(&e->d_acc, accs, s)) != cudaSuccess) return done(ce);
+  if ((ce = upload(&e->d_offs, offs, s)) != cudaSuccess) return done(ce);
+  if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) return done(ce);
+  // capture
+  const csrc_matrix_s* h0 = batch > 0 ? hs[0] : nullptr;
+  if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return done(ce);
+  cudaError_t cap = cudaSuccess;
+  for (auto& z : zero_y)
+    if (cap == cudaSuccess) cap = cudaMemsetAsync(z.first, 0, z.second, s);
+  if (cap == cudaSuccess && !launches.empty()) cap = cudaMemsetAsync(e->d_counters, 0, launches.size() * 4, s);
+  for (size_t i = 0; i < launches.size() && cap == cudaSuccess; ++i) {
+    const Launch& L = launches[i];
+    const int grid = std::min(L.count, sms * BandShape<MODE_DF>::kCtasPerSm);
+    cap = launch_batch_band(h0->arith, h0->storage, L.group, L.atomic, grid, smem, s, e->d_members,
+                            e->d_tiles + L.first, L.count, e->d_counters + i);
+    ++e->kernels;
+  }
+  if (cap == cudaSuccess && offs.back() > 0) {
+    cap = launch_batch_accumulate(h0->storage, e->d_acc, e->d_offs, (int)accs.size(), offs.back(), s);
+    ++e->kernels;
+  }
+  ce = cudaStreamEndCapture(s, &e->graph);
+  if (cap != cudaSuccess) return done(cap);
+  if (ce != cudaSuccess) return done(ce);
+  if ((ce = cudaGraphInstantiate(&e->exec, e->graph, 0)) != cudaSuccess) return done(ce);
+  *out = e;
+  return done(cudaSuccess);
+}
+
+csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int transpose,
+                      cudaStream_t stream) {
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return CSRC_ERR_CUDA;
+  for (int32_t b = 0; b < batch; ++b)
+    if (hs[b]->device != device) return CSRC_ERR_INVALID_ARG;  // one device per batch
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  BatchExec* e = nullptr;
+  for (size_t i = 0; i < g_batches.size(); ++i)
+    if (batch_matches(g_batches[i], hs, batch, X, Y, transpose, device)) {
+      e = g_batches[i];
+      g_batches.erase(g_batches.begin() + (long)i);
+      g_batches.push_back(e);
+      break;
+    }
+  if (!e) {
+    CSRC_TRY_S(build_batch(hs, batch, X, Y, transpose, device, &e));
+    if (g_batches.size() >= kMaxBatches) {
+      delete g_batches.front();
+      g_batches.erase(g_batches.begin());
+    }
+    g_batches.push_back(e);
+  }
+  csrc_matrix_s* h0 = hs[0];
+  return from_cuda(timed_launch(h0, CSRC_KERNEL_PRODUCT, stream, [&] { return cudaGraphLaunch(e->exec, stream); },
+                                e->kernels));
+}
+
 csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
                                  const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream) {
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
@@ -769,7 +965,7 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   {
     std::lock_guard<std::mutex> lk(g_setup_mutex);
     if (!g_prepared) {
-      if (prepare_band_kernels() != cudaSuccess) {
+      if (prepare_band_kernels() != cudaSuccess || prepare_batch_kernels() != cudaSuccess) {
         cudaGetLastError();
         return fail(CSRC_ERR_CUDA);
       }
@@ -996,7 +1192,9 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
     if (!hs[b] || !X[b] || !Y[b]) return CSRC_ERR_INVALID_ARG;
     if (hs[b]->storage != hs[0]->storage) return CSRC_ERR_MISMATCH;
   }
+  if (batch == 0) return CSRC_OK;
   try {
+    if (nrhs == 1) return run_batch(hs, batch, X, Y, transpose != 0 ? 1 : 0, stream);
     for (int32_t b = 0; b < batch; ++b) CSRC_TRY_S(spmm_one(hs[b], X[b], Y[b], nrhs, transpose != 0, stream));
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
@@ -1032,7 +1230,7 @@ csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out) {
       break;
     }
     if (t.kind >= 0 && t.kind < CSRC_KERNEL_KINDS) {
-      out->launches[t.kind] += 1;
+      out->launches[t.kind] += t.kernels;
       out->ms[t.kind] += ms;
     }
   }
@@ -1080,6 +1278,7 @@ csrc_status csrc_get_last_device_error(csrc_handle h) {
 
 csrc_status csrc_destroy(csrc_handle h) {
   if (!h) return CSRC_OK;
+  drop_batches_of(h);
   ensure_device(h);
   cudaDeviceSynchronize();
   free_plan(h->plan);

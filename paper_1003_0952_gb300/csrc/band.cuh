@@ -61,6 +61,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -193,8 +197,12 @@ struct RowX<MODE_DF> {
 
 
 // ---------------------------------------------------------------------------- the band kernel
+// One band b of the product described by a, run by the whole CTA. The CTA may run
+// several bands one after another (the batched kernel): its mbarriers are initialised at
+// the start and invalidated at the end. Returns false when a bounded wait ran out (the
+// status word says so and the CTA must not run further bands).
 template <int MODE, int G, bool ATOMIC, int RK>
-__global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
+__device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   using Sh = BandShape<MODE>;
   using V = typename Traits<MODE>::V;
   using X = typename Traits<MODE>::X;
@@ -210,7 +218,6 @@ __global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerS
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int b = blockIdx.x + a.band_offset;
   const int r0 = a.band_row[b];
   const int r1 = a.band_row[b + 1];
   const int plo = a.band_plo[b];
@@ -509,6 +516,7 @@ __global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerS
 
   // ---- a wait ran out (should not happen): let this CTA's copies land, then stop
   __shared__ int abort_flag;
+  __syncthreads();
   if (tid == 0) abort_flag = 0;
   __syncthreads();
   if (timed_out) abort_flag = 1;
@@ -519,7 +527,11 @@ __global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerS
       for (int s = 0; s < issued; ++s) mbar_wait(bar_full + 8u * (s % NS), (uint32_t)((s / NS) & 1));
       atomicOr(a.status, DEV_TIMEOUT);
     }
-    return;
+    return false;
+  }
+  // every copy has landed and every wait has completed: the barriers can be retired
+  if (tid == 0) {
+    for (int i = 0; i < 2 * NS + 1; ++i) mbar_inval(smem_addr(bars + i));
   }
 
   // ---- phase 3: own rows (the diagonal term is added here, so rows without pairs are covered)
@@ -565,6 +577,13 @@ __global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerS
     }
   }
   if (bad) atomicOr(a.status, (int)((bad & 1u) ? DEV_RANGE : 0) | (int)((bad & 4u) ? DEV_BOUNDS : 0));
+  __syncthreads();  // the next band of this CTA reuses the shared memory
+  return true;
+}
+
+template <int MODE, int G, bool ATOMIC, int RK>
+__global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
+  band_body<MODE, G, ATOMIC, RK>(a, blockIdx.x + a.band_offset);
 }
 
 // Dynamic shared memory limit of one instantiation.

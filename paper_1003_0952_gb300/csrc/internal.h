@@ -134,6 +134,7 @@ struct DevPlan {
   int32_t max_slots = 0;
   int32_t max_tab = 0;
   int32_t smem_bytes = 0;      // dynamic shared memory of a band CTA (ring + window + table)
+  std::vector<int64_t> band_pairs;  // host copy: stored pairs of each band (batched scheduling)
   int64_t total_pages = 0;
 };
 
@@ -166,6 +167,15 @@ struct BandArgs {
   int32_t band_offset;
 };
 
+// Accumulation arguments of one batch member (spill -> y).
+struct AccArgs {
+  const int32_t* acc_row;
+  const int32_t* acc_ptr;
+  const int32_t* acc_src;
+  const void* spill;
+  void* y;
+};
+
 // Device status bits (OR-ed by kernels, read by csrc_get_last_device_error).
 enum : int32_t { DEV_RANGE = 1, DEV_TIMEOUT = 2, DEV_BOUNDS = 4 };
 
@@ -178,6 +188,13 @@ cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, in
                               cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
+
+// Batched products (batch.cu).
+cudaError_t prepare_batch_kernels();
+cudaError_t launch_batch_band(Arith arith, int storage, int group, bool atomic, int grid, int smem, cudaStream_t s,
+                              const BandArgs* members, const int2* tiles, int ntiles, int* next_tile);
+cudaError_t launch_batch_accumulate(int storage, const AccArgs* members, const int64_t* offs, int nmembers,
+                                    int64_t total, cudaStream_t s);
 
 // Product into caller-provided spill memory, allocating nothing (api.cpp; used by noalloc.cu).
 int32_t handle_device(const csrc_matrix_s* h);

@@ -114,3 +114,64 @@ def test_spmm_batch_of_uneven_members(cs):
     finally:
         for h in hs:
             cs.csrc_destroy(h)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_batched_single_vectors_graph_replay(cs, storage):
+    # one persistent launch over all members' bands, captured in a CUDA graph and replayed
+    ms = fe.batch_meshes(12, 77, nmin=50, nmax=30000)
+    hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage]) for m in ms]
+    dt = torch.float64 if storage == "f64" else torch.float32
+    try:
+        xs = [fe.source_vector(m.n, 100 + i) for i, m in enumerate(ms)]
+        if storage != "f64":
+            xs = [x.astype(np.float32).astype(np.float64) for x in xs]
+        Xd = [torch.from_numpy(x).to(dt).cuda() for x in xs]
+        Yd = [torch.full_like(x, float("nan")) for x in Xd]
+        tol = 1e-12 if storage == "f64" else 1e-5
+        for rep in range(3):  # first call builds the graph, the others replay it
+            for tr in (False, True):
+                for y in Yd:
+                    y.fill_(float("nan"))
+                cs.csrc_spmm_batched(hs, Xd, Yd, 1, tr, torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                for m, x, y, h in zip(ms, xs, Yd, hs):
+                    c = oracle.from_matrix(m)
+                    yref = (oracle.csrc_spmv_t if tr else oracle.csrc_spmv)(c, x)
+                    mm = _transpose(m) if tr else m
+                    assert oracle.max_rel_err(mm, x, y.cpu().numpy().astype(np.float64), yref) <= tol
+                    assert cs.csrc_get_last_device_error(h) == cs.CSRC_OK
+        # new output buffers: a new graph
+        Yd2 = [torch.empty_like(x) for x in Xd]
+        cs.csrc_spmm_batched(hs, Xd, Yd2, 1, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for m, x, y in zip(ms, xs, Yd2):
+            yref = oracle.csrc_spmv(oracle.from_matrix(m), x)
+            assert oracle.max_rel_err(m, x, y.cpu().numpy().astype(np.float64), yref) <= tol
+    finally:
+        for h in hs:
+            cs.csrc_destroy(h)
+
+
+def test_batched_integer_exact_and_mismatch(cs):
+    ms = [fe.p1_grid(11, 9, 1), fe.q1_hex(5, 3, 2), fe.tet_mesh(1500, 3, method="kuhn")]
+    ims = [fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 5)) for m in ms]
+    hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64) for m in ims]
+    try:
+        xs = [fe.integer_vector(m.n, 6 + i) for i, m in enumerate(ims)]
+        Xd = [torch.from_numpy(x).cuda() for x in xs]
+        Yd = [torch.empty_like(x) for x in Xd]
+        cs.csrc_spmm_batched(hs, Xd, Yd, 1, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for m, x, y in zip(ims, xs, Yd):
+            np.testing.assert_array_equal(y.cpu().numpy(), oracle.csrc_spmv(oracle.from_matrix(m), x))
+        h32 = cs.csrc_create_from_csr(ims[0].n, ims[0].row_ptr, ims[0].col, ims[0].val, cs.CSRC_F32)
+        try:
+            with pytest.raises(cs.CsrcError) as e:
+                cs.csrc_spmm_batched([hs[0], h32], Xd[:1] * 2, Yd[:1] * 2, 1, False)
+            assert e.value.status == cs.CSRC_ERR_MISMATCH
+        finally:
+            cs.csrc_destroy(h32)
+    finally:
+        for h in hs:
+            cs.csrc_destroy(h)
