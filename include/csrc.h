@@ -97,6 +97,9 @@ typedef struct {
   int32_t smem_bytes;       /* dynamic shared memory of the band kernel */
   int32_t ncolors;          /* colours (0 before csrc_color) */
   int32_t tuned_strategy;   /* csrc_strategy picked by csrc_autotune (0 = not tuned) */
+  int32_t tuned_rk;         /* columns per pass picked by csrc_autotune_spmm (0 = up to 8) */
+  int32_t group;            /* lanes per row of the band kernel (0 before the plan is built) */
+  int64_t nstages;          /* shared-memory ring stages of one single-vector product */
 } csrc_info;
 
 /*
@@ -207,9 +210,25 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
  */
 csrc_status csrc_spmv_noalloc(csrc_handle h, const void* x, void* y, int32_t transpose, cudaStream_t stream);
 
-/* Time the strategies on this handle (stream-ordered, synchronous) and keep the
- * fastest one as its CSRC_STRAT_AUTO choice. x and y are device scratch vectors of n elements. */
+/*
+ * Autotuner (not in the paper, whose comparison of colouring and local buffers in
+ * Section 4.2 shows that the best strategy depends on the matrix). Times y = A x with
+ * every applicable strategy (window, atomic, and colour when csrc_color has run) and
+ * several band counts (automatic, one and four per SM), then keeps the fastest band
+ * count as the handle's partition and the fastest strategy as its CSRC_STRAT_AUTO
+ * choice; batched products use it per member. Synchronous on stream.
+ *   x, y  device vectors of n elements used as scratch (y is overwritten)
+ * Errors: INVALID_ARG (null or host pointers), OUT_OF_MEMORY, CUDA.
+ */
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream);
+
+/*
+ * Pick the columns per pass (2, 4 or 8) of several-right-hand-side products on this
+ * handle by timing Y = A X on the caller's n-by-nrhs row-major device blocks X and Y
+ * (Y is overwritten). Synchronous on stream. nrhs = 1 leaves the handle unchanged.
+ * Errors: INVALID_ARG, NOT_PARTITIONED, OUT_OF_MEMORY, CUDA.
+ */
+csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream);
 
 /* Kernel kinds of csrc_kernel_times. */
 enum {

@@ -59,6 +59,7 @@ class csrc_info(ctypes.Structure):
         ("nbands", ctypes.c_int32), ("page_rows", ctypes.c_int32), ("spill_entries", ctypes.c_int64),
         ("spill_rows", ctypes.c_int64), ("accum_bytes", ctypes.c_int64), ("max_window_slots", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("tuned_strategy", ctypes.c_int32),
+        ("tuned_rk", ctypes.c_int32), ("group", ctypes.c_int32), ("nstages", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -89,6 +90,7 @@ SIGNATURES = {
                                          _VP]),
     "csrc_spmv_noalloc": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "csrc_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "csrc_autotune_spmm": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP]),
     "csrc_set_profiling": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "csrc_get_kernel_times": (ctypes.c_int, [_VP, _P(csrc_kernel_times)]),
     "csrc_get_info": (ctypes.c_int, [_VP, _P(csrc_info)]),
@@ -225,6 +227,10 @@ def csrc_get_kernel_times(h) -> dict:
     t = csrc_kernel_times()
     _check(_lib.csrc_get_kernel_times(h, ctypes.byref(t)), "csrc_get_kernel_times")
     return {k: (int(t.launches[i]), float(t.ms[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def csrc_autotune_spmm(h, X, Y, nrhs, stream=None) -> None:
+    _check(_lib.csrc_autotune_spmm(h, _ptr(X), _ptr(Y), int(nrhs), _stream(stream)), "csrc_autotune_spmm")
 
 
 def csrc_get_info(h) -> dict:

@@ -1204,9 +1204,100 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
 
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream) {
   if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
-  (void)stream;
-  h->tuned = CSRC_STRAT_WINDOW;
-  return CSRC_OK;
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  if (h->n == 0) {
+    h->tuned = CSRC_STRAT_WINDOW;
+    return CSRC_OK;
+  }
+  try {
+    const bool prof = h->profiling;
+    h->profiling = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CSRC_TRY(cudaEventCreate(&e0));
+    CSRC_TRY(cudaEventCreate(&e1));
+    auto time_it = [&](csrc_strategy st, float* ms) -> csrc_status {
+      CSRC_TRY_S(run_spmv(h, x, y, st, stream, false));  // warm-up
+      CSRC_TRY(cudaEventRecord(e0, stream));
+      for (int i = 0; i < 3; ++i) CSRC_TRY_S(run_spmv(h, x, y, st, stream, false));
+      CSRC_TRY(cudaEventRecord(e1, stream));
+      CSRC_TRY(cudaEventSynchronize(e1));
+      CSRC_TRY(cudaEventElapsedTime(ms, e0, e1));
+      return CSRC_OK;
+    };
+    // band counts: the automatic choice, one band per SM, and four per SM (windows split further as needed)
+    const int32_t counts[3] = {0, h->sms, 4 * h->sms};
+    float best = 1e30f;
+    int32_t best_nb = 0, best_st = CSRC_STRAT_WINDOW;
+    csrc_status st = CSRC_OK;
+    for (int32_t nb : counts) {
+      if (nb > h->n) continue;
+      if ((st = make_plan(h, nb)) != CSRC_OK) break;
+      const csrc_strategy cands[3] = {CSRC_STRAT_WINDOW, CSRC_STRAT_ATOMIC, CSRC_STRAT_COLOR};
+      for (csrc_strategy c : cands) {
+        if (c == CSRC_STRAT_WINDOW && !h->plan_covers) continue;
+        if (c == CSRC_STRAT_COLOR && (h->ncolors == 0 || nb != 0)) continue;  // colouring does not use bands
+        float ms = 0.f;
+        if ((st = time_it(c, &ms)) != CSRC_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_nb = nb;
+          best_st = c;
+        }
+      }
+      if (st != CSRC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->profiling = prof;
+    if (st != CSRC_OK) return st;
+    CSRC_TRY_S(make_plan(h, best_nb));
+    h->tuned = best_st;
+    ++h->generation;
+    return CSRC_OK;
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream) {
+  if (!h || !X || !Y || nrhs <= 0) return CSRC_ERR_INVALID_ARG;
+  CSRC_TRY_S(ensure_device(h));
+  if (h->n == 0 || nrhs == 1) return CSRC_OK;
+  try {
+    const bool prof = h->profiling;
+    h->profiling = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CSRC_TRY(cudaEventCreate(&e0));
+    CSRC_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int32_t best_rk = 0;
+    csrc_status st = CSRC_OK;
+    for (int32_t rk = 2; rk <= 8 && st == CSRC_OK; rk *= 2) {
+      if (rk > nrhs) break;
+      h->tuned_rk = rk;
+      if ((st = spmm_one(h, X, Y, nrhs, false, stream)) != CSRC_OK) break;  // warm-up (builds the plan)
+      float ms = 0.f;
+      cudaError_t ce = cudaEventRecord(e0, stream);
+      for (int i = 0; i < 3 && st == CSRC_OK && ce == cudaSuccess; ++i) st = spmm_one(h, X, Y, nrhs, false, stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, stream);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) st = from_cuda(ce);
+      if (st == CSRC_OK && ms < best) {
+        best = ms;
+        best_rk = rk;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->profiling = prof;
+    h->tuned_rk = best_rk;
+    ++h->generation;
+    return st;
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
 }
 
 csrc_status csrc_set_profiling(csrc_handle h, int32_t enable) {
@@ -1260,6 +1351,9 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   }
   info->ncolors = h->ncolors;
   info->tuned_strategy = h->tuned;
+  info->tuned_rk = h->tuned_rk;
+  info->group = h->have_plan ? h->plan.group : 0;
+  info->nstages = h->have_plan ? h->plan.nstages : 0;
   return CSRC_OK;
 }
 

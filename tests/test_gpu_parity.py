@@ -366,3 +366,20 @@ def test_full_size_q1(cs, name):
             assert oracle.max_rel_err(mt, x, y, oracle.csr_spmv(m.n, mt.row_ptr, mt.col, mt.val, x)) <= TOL["f64"]
     finally:
         h.close()
+
+
+# --------------------------------------------------------------------------- autotuner
+def test_autotune_picks_a_strategy_and_stays_correct(cs):
+    m = fe.q1_hex(16, 3, 44)
+    x = fe.source_vector(m.n, 45)
+    h = Handle(cs, m, seed=9)  # coloured, so the colour strategy is a candidate too
+    try:
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        cs.csrc_autotune(h.h, xd, yd, torch.cuda.current_stream())
+        info = cs.csrc_get_info(h.h)
+        assert info["tuned_strategy"] in (cs.CSRC_STRAT_WINDOW, cs.CSRC_STRAT_COLOR, cs.CSRC_STRAT_ATOMIC)
+        for tr in (False, True):
+            _check(m, x, h.run(x, "auto", tr), tr, TOL["f64"])
+    finally:
+        h.close()

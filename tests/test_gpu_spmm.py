@@ -175,3 +175,19 @@ def test_batched_integer_exact_and_mismatch(cs):
     finally:
         for h in hs:
             cs.csrc_destroy(h)
+
+
+def test_autotune_spmm_k_tile(cs):
+    m = fe.q1_hex(11, 1, 12)
+    c = oracle.from_matrix(m)
+    X = fe.source_vector(m.n, 13, nrhs=16)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        Xd = torch.from_numpy(X).cuda()
+        Yd = torch.empty_like(Xd)
+        cs.csrc_autotune_spmm(h, Xd, Yd, 16, torch.cuda.current_stream())
+        assert cs.csrc_get_info(h)["tuned_rk"] in (2, 4, 8)
+        Y = _run(cs, h, X, "f64", False)
+        assert oracle.max_rel_err(m, X, Y, oracle.csrc_spmm(c, X)) <= 1e-12
+    finally:
+        cs.csrc_destroy(h)
