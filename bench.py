@@ -379,6 +379,148 @@ def run_ours(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- suite of every configuration
+def _events_ms(fn, iters: int) -> float:
+    import torch
+
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(iters):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def run_suite(args):
+    """One JSON line per configuration row: FP64 strategies, FP32 / BF16 storage, several
+    right-hand sides and the batched graph launch. Device time with CUDA events; every
+    row's inputs are larger than L2 except the P1 100x100 one (marked)."""
+    import torch
+
+    import fe_inputs as fe
+    import paper_1003_0952_gb300 as cs
+
+    torch.cuda.set_device(0)
+    peak, _ = measured_hbm()
+    st = torch.cuda.current_stream()
+    sptr = st.cuda_stream
+
+    def emit(d):
+        d["frac_of_measured_hbm"] = d["GB/s"] / peak if "GB/s" in d else None
+        print(json.dumps(d), flush=True)
+
+    def spmv_rows(name, m, storages, strategies, colour=False):
+        xs = fe.source_vector(m.n, 7)
+        for storage in storages:
+            vb = {"f64": 8, "f32": 4, "bf16": 2}[storage]
+            xb = 8 if storage == "f64" else 4
+            h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+            try:
+                cs.csrc_partition(h, 0)
+                if colour:
+                    cs.csrc_color(h, 12345)
+                dt = torch.float64 if storage == "f64" else torch.float32
+                x = torch.from_numpy(xs).to(dt).cuda()
+                y = torch.empty_like(x)
+                mb = model_bytes(m.n, m.pairs, vb, xb)
+                for strat in strategies:
+                    if strat == "color" and not colour:
+                        continue
+                    code = cs.STRATEGIES[strat]
+                    ms = _events_ms(lambda: (cs.csrc_spmv(h, x, y, code, sptr), cs.csrc_spmv_t(h, x, y, code, sptr)),
+                                    args.suite_iters) / 2
+                    info = cs.csrc_get_info(h)
+                    emit({"suite": name, "n": m.n, "nnz": m.nnz, "storage": storage, "strategy": strat,
+                          "ms_per_product": ms, "GB/s": mb / ms / 1e6, "GFLOP/s": flops(m.n, m.pairs) / ms / 1e6,
+                          "nbands": info["nbands"], "spill_entries": info["spill_entries"],
+                          "ncolors": info["ncolors"], "lanes_per_row": info["group"]})
+                if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
+                    raise RuntimeError("device status")
+            finally:
+                cs.csrc_destroy(h)
+
+    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5"}
+    if "c1" in sel:
+        m, _ = build_workload("p1_100x100")
+        spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
+    if "c2" in sel:
+        for wl in ("q1s_96", "q1v_96"):
+            m, _ = build_workload(wl)
+            spmv_rows(f"C2 {wl}", m, ["f64"], ["window", "atomic", "color"], colour=True)
+            del m
+    if "c3" in sel:
+        m = fe.tet_mesh(2_000_000, 1003, method=args.tet_method)
+        spmv_rows(f"C3 tet_{args.tet_method}_2m", m, ["f64", "f32"], ["window"])
+        del m
+    if "c4" in sel:
+        m, _ = build_workload("q1s_96")
+        for storage in ("f64", "bf16"):
+            vb = {"f64": 8, "bf16": 2}[storage]
+            xb = 8 if storage == "f64" else 4
+            h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+            try:
+                cs.csrc_partition(h, 0)
+                dt = torch.float64 if storage == "f64" else torch.float32
+                for r in (4, 8, 16, 32):
+                    X = torch.from_numpy(fe.source_vector(m.n, 8, nrhs=r)).to(dt).cuda()
+                    Y = torch.empty_like(X)
+                    cs.csrc_autotune_spmm(h, X, Y, r, sptr)
+                    rk = cs.csrc_get_info(h)["tuned_rk"]
+                    ms = _events_ms(lambda: cs.csrc_spmm_batched([h], [X], [Y], r, False, sptr), args.suite_iters)
+                    matrix = 4 * (m.n + 1) + 4 * m.pairs + 2 * vb * m.pairs + vb * m.n
+                    mb = matrix + 2 * r * m.n * xb
+                    passes = (r + rk - 1) // rk if rk else 1
+                    emit({"suite": "C4 q1s_96 several right-hand sides", "storage": storage, "nrhs": r,
+                          "k_tile": rk, "ms": ms, "GB/s": mb / ms / 1e6,
+                          "GFLOP/s": r * flops(m.n, m.pairs) / ms / 1e6,
+                          "streamed_GB/s": (passes * matrix + 2 * r * m.n * xb) / ms / 1e6})
+                    del X, Y
+            finally:
+                cs.csrc_destroy(h)
+        del m
+    if "c5" in sel:
+        ms_list = fe.batch_meshes(256, 1005)
+        tot_n = sum(m.n for m in ms_list)
+        tot_pairs = sum(m.pairs for m in ms_list)
+        res = {}
+        for storage in ("f32", "f64"):
+            hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage]) for m in ms_list]
+            try:
+                dt = torch.float64 if storage == "f64" else torch.float32
+                X = [torch.from_numpy(fe.source_vector(m.n, 9 + i)).to(dt).cuda() for i, m in enumerate(ms_list)]
+                Y = [torch.empty_like(x) for x in X]
+                if storage == "f32":
+                    for h, x, y in zip(hs, X, Y):
+                        cs.csrc_autotune(h, x, y, sptr)
+                    ms = _events_ms(lambda: cs.csrc_spmm_batched(hs, X, Y, 1, False, sptr), args.suite_iters)
+                    vb, xb, how = 4, 4, "one CUDA-graph replay: persistent band kernels over all 256 members"
+                else:
+                    for h in hs:
+                        cs.csrc_partition(h, 0)
+
+                    def separate():
+                        for h, x, y in zip(hs, X, Y):
+                            cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr)
+
+                    ms = _events_ms(separate, max(3, args.suite_iters // 4))
+                    vb, xb, how = 8, 8, "256 separate csrc_spmv calls (band + accumulation launches each)"
+                mb = sum(model_bytes(m.n, m.pairs, vb, xb) for m in ms_list)
+                res[storage] = ms
+                emit({"suite": "C5 batch_256", "storage": storage, "how": how, "members": len(ms_list),
+                      "sum_n": tot_n, "sum_pairs": tot_pairs, "ms_per_batch": ms, "GB/s": mb / ms / 1e6,
+                      "GFLOP/s": flops(tot_n, tot_pairs) / ms / 1e6})
+            finally:
+                for h in hs:
+                    cs.csrc_destroy(h)
+        emit({"suite": "C5 batch_256 speedup", "f32_graph_vs_f64_separate": res["f64"] / res["f32"]})
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +533,12 @@ def main(argv=None):
                     help="value storage: f64 (the default workload), or f32 / bf16 with float vectors")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", default=None, help="all, or a comma list of c1..c5: one JSON line per configuration row")
+    ap.add_argument("--suite-iters", type=int, default=20)
+    ap.add_argument("--tet-method", default="delaunay", choices=["delaunay", "kuhn"])
     args = ap.parse_args(argv)
+    if args.suite:
+        return run_suite(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

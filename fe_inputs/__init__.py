@@ -16,6 +16,8 @@ from .generators import (  # noqa: F401
     pattern_from_edges,
     p1_triangle_grid_edges,
     kuhn_tet_grid_edges,
+    p1_triangle_grid_pattern,
+    kuhn_tet_grid_pattern,
     q1_hex27_pattern,
     delaunay_edges,
     permute_pattern,

@@ -157,6 +157,40 @@ def q1_hex27_pattern(nx: int, ny: int, nz: int):
     return row_ptr, col
 
 
+def _stencil_pattern(dims, offsets):
+    """Full CSR pattern of a structured grid stencil: node id = (iz*ny + iy)*nx + ix,
+    neighbours at the given (dx, dy, dz) offsets (the centre included), columns ascending."""
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    ids = np.arange(n, dtype=np.int64)
+    ix = ids % nx
+    iy = (ids // nx) % ny
+    iz = ids // (nx * ny)
+    offs = sorted(offsets, key=lambda o: o[0] + o[1] * nx + o[2] * nx * ny)  # ascending column id
+    cols = np.empty((n, len(offs)), dtype=np.int64)
+    for q, (dx, dy, dz) in enumerate(offs):
+        ok = ((ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny) & (iz + dz >= 0) & (iz + dz < nz))
+        cols[:, q] = np.where(ok, ids + dx + dy * nx + dz * nx * ny, -1)
+    mask = cols >= 0
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(mask.sum(axis=1), out=row_ptr[1:])
+    return row_ptr, cols[mask].astype(np.int32)
+
+
+def p1_triangle_grid_pattern(nx: int, ny: int):
+    """The pattern of p1_triangle_grid_edges (plus the diagonal), built directly in CSR form."""
+    d = [(1, 0, 0), (0, 1, 0), (1, 1, 0)]
+    offs = [(0, 0, 0)] + d + [(-a, -b, -c) for a, b, c in d]
+    return _stencil_pattern((nx, ny, 1), offs)
+
+
+def kuhn_tet_grid_pattern(nx: int, ny: int, nz: int):
+    """The pattern of kuhn_tet_grid_edges (plus the diagonal), built directly in CSR form."""
+    d = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+    offs = [(0, 0, 0)] + d + [(-a, -b, -c) for a, b, c in d]
+    return _stencil_pattern((nx, ny, nz), offs)
+
+
 def delaunay_edges(npts: int, seed: int):
     """Edges of the Delaunay tetrahedralisation of npts uniform points in the unit cube."""
     from scipy.spatial import Delaunay
@@ -380,15 +414,14 @@ def batch_meshes(count: int = 256, seed: int = 1005, nmin: int = 2000, nmax: int
         target = math.exp(rng.uniform(math.log(nmin), math.log(nmax)))
         if rng.random() < 0.5:
             side = max(2, int(round(math.sqrt(target))))
-            ei, ej = p1_triangle_grid_edges(side, side)
+            rp, c = p1_triangle_grid_pattern(side, side)
             n = side * side
             kind = "p1"
         else:
             side = max(2, int(round(target ** (1.0 / 3.0))))
-            ei, ej = kuhn_tet_grid_edges(side, side, side)
+            rp, c = kuhn_tet_grid_pattern(side, side, side)
             n = side ** 3
             kind = "kuhn"
-        rp, c = pattern_from_edges(n, ei, ej)
         val = random_fe_values(rp, c, seed * 100003 + b)
         out.append(FEMatrix(n, rp, c, val, f"batch{b}_{kind}_{n}", {"kind": kind, "side": side}))
     return out

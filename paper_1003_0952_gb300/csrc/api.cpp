@@ -43,6 +43,7 @@ struct csrc_matrix_s {
   DevPlan plan_rk[3];
   bool have_rk[3] = {false, false, false};
   bool covers_rk[3] = {false, false, false};
+  bool fits_rk[3] = {false, false, false};
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -444,9 +445,17 @@ csrc_status plan_for(csrc_matrix_s* h, int rk, DevPlan** out, bool* covers) {
   }
   const int i = rk == 2 ? 0 : (rk == 4 ? 1 : 2);
   if (!h->have_rk[i]) {
-    CSRC_TRY_S(build_plan(h, h->part_nbands, rk, h->plan_rk[i], h->covers_rk[i], nullptr));
+    const csrc_status st = build_plan(h, h->part_nbands, rk, h->plan_rk[i], h->covers_rk[i], nullptr);
+    if (st == CSRC_ERR_NOT_PARTITIONED) {
+      h->have_rk[i] = true;  // remembered: no window of rk columns fits this matrix
+      h->fits_rk[i] = false;
+      return st;
+    }
+    CSRC_TRY_S(st);
     h->have_rk[i] = true;
+    h->fits_rk[i] = true;
   }
+  if (!h->fits_rk[i]) return CSRC_ERR_NOT_PARTITIONED;
   *out = &h->plan_rk[i];
   *covers = h->covers_rk[i];
   return CSRC_OK;
@@ -610,16 +619,26 @@ csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, boo
   for (int32_t c0 = 0; c0 < nrhs;) {
     int rk = 8;
     while (rk > 1 && (rk > cap || c0 + rk > nrhs)) rk /= 2;
+    // a wider pass needs a wider window: when no band of rk columns fits in shared
+    // memory, fall back to fewer columns per pass
     DevPlan* p = nullptr;
     bool covers = false;
-    CSRC_TRY_S(plan_for(h, rk, &p, &covers));
-    if (!covers) return CSRC_ERR_NOT_PARTITIONED;
+    while (true) {
+      const csrc_status st = plan_for(h, rk, &p, &covers);
+      if (st == CSRC_OK && (covers || rk == 1)) break;
+      if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
+      if (rk == 1) return st;
+      rk /= 2;
+    }
     const void* xc = static_cast<const char*>(X) + (size_t)c0 * h->xbytes();
     void* yc = static_cast<char*>(Y) + (size_t)c0 * h->xbytes();
+    const bool atomic = !covers;  // single column whose plan overflows: atomic strategy
+    if (atomic)
+      CSRC_TRY(cudaMemset2DAsync(yc, (size_t)nrhs * h->xbytes(), 0, h->xbytes(), (size_t)h->n, s));
     const BandArgs a = band_args(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk);
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
-                          [&] { return launch_band(h->arith, h->storage, false, a, p->nb, p->smem_bytes, s); }));
-    if (p->nacc > 0)
+                          [&] { return launch_band(h->arith, h->storage, atomic, a, p->nb, p->smem_bytes, s); }));
+    if (!atomic && p->nacc > 0)
       CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
         return launch_accumulate(h->arith, h->storage, p->nacc, rk, nrhs, p->acc_row, p->acc_ptr, p->acc_src,
                                  p->spill_buf, yc, s);
@@ -1121,20 +1140,20 @@ csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32
     cudaError_t e = upload(&d_up_ptr, up_ptr, s);
     if (e == cudaSuccess) e = upload(&d_up, up, s);
     if (e == cudaSuccess) e = dmalloc(&d_state, (size_t)n);
-    if (e == cudaSuccess) e = dmalloc(&d_cnt, 1);
+    if (e == cudaSuccess) e = dmalloc(&d_cnt, 2);  // uncoloured rows, too-many-colours flag
     if (e == cudaSuccess) e = cudaMemsetAsync(d_state, 0xff, (size_t)n * 4, s);
     int32_t round = 0;
-    int32_t left = n;
-    while (e == cudaSuccess && left > 0) {
+    int32_t left[2] = {n, 0};
+    while (e == cudaSuccess && left[0] > 0) {
       ++round;
       if (round >= 32768) {
         cleanup();
         return CSRC_ERR_DEVICE_TIMEOUT;
       }
-      e = cudaMemsetAsync(d_cnt, 0, 4, s);
+      e = cudaMemsetAsync(d_cnt, 0, 8, s);
       if (e == cudaSuccess) e = launch_jp_round(n, h->d_ia, h->d_ja, d_up_ptr, d_up, seed, round, d_state, d_cnt, s);
-      if (e == cudaSuccess) e = cudaMemcpy(&left, d_cnt, 4, cudaMemcpyDeviceToHost);
-      if (e == cudaSuccess && left >= (1 << 20)) {
+      if (e == cudaSuccess) e = cudaMemcpy(left, d_cnt, 8, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess && left[1] != 0) {
         cleanup();
         return CSRC_ERR_INVALID_ARG;  // more than 65536 colours
       }
@@ -1275,8 +1294,16 @@ csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nr
     csrc_status st = CSRC_OK;
     for (int32_t rk = 2; rk <= 8 && st == CSRC_OK; rk *= 2) {
       if (rk > nrhs) break;
+      DevPlan* p = nullptr;
+      bool covers = false;
+      const csrc_status ps = plan_for(h, rk, &p, &covers);
+      if (ps == CSRC_ERR_NOT_PARTITIONED || (ps == CSRC_OK && !covers)) break;  // wider passes fit even less
+      if (ps != CSRC_OK) {
+        st = ps;
+        break;
+      }
       h->tuned_rk = rk;
-      if ((st = spmm_one(h, X, Y, nrhs, false, stream)) != CSRC_OK) break;  // warm-up (builds the plan)
+      if ((st = spmm_one(h, X, Y, nrhs, false, stream)) != CSRC_OK) break;  // warm-up
       float ms = 0.f;
       cudaError_t ce = cudaEventRecord(e0, stream);
       for (int i = 0; i < 3 && st == CSRC_OK && ce == cudaSuccess; ++i) st = spmm_one(h, X, Y, nrhs, false, stream);

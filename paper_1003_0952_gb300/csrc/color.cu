@@ -6,6 +6,9 @@
 // walking t in W(u) and, for each t, the row t itself and the rows of A_U's
 // column t: the rows v > t with t in their ja, listed in (up_ptr, up).
 //
+// uncolored[0] counts the rows left uncoloured by a round; uncolored[1] is set when a
+// row would need more than 65536 colours.
+//
 // Jones-Plassmann: in every round, each uncoloured row that outranks all its
 // uncoloured neighbours (priority SplitMix64(seed ^ row)) takes the smallest
 // colour unused by its coloured neighbours. Adjacent rows are never both local
@@ -80,7 +83,8 @@ __global__ void jp_round_kernel(int32_t n, const int32_t* __restrict__ ia, const
       return;
     }
   }
-  atomicAdd(uncolored, 1 << 20);  // more than 65536 colours: reported as a failure by the host
+  atomicAdd(uncolored, 1);
+  atomicOr(uncolored + 1, 1);  // more than 65536 colours: the host reports a failure
 }
 
 cudaError_t launch_jp_round(int32_t n, const int32_t* ia, const int32_t* ja, const int32_t* up_ptr, const int32_t* up,
