@@ -76,8 +76,10 @@ typedef enum {
 enum {
   CSRC_FLAG_PAD_PATTERN = 1, /* add an explicit zero a_ji for every a_ij without a mirror */
   CSRC_FLAG_ONE_BASED = 2,   /* row_ptr / row / col are 1-based (Fortran, as in Fig. 2) */
-  CSRC_FLAG_FP64_ARITH = 4   /* CSRC_F64 only: multiply and add on the FP64 pipe (bit-for-bit IEEE
+  CSRC_FLAG_FP64_ARITH = 4,  /* CSRC_F64 only: multiply and add on the FP64 pipe (bit-for-bit IEEE
                                 double products) instead of the default double-float arithmetic */
+  CSRC_FLAG_NODE_BLOCKS = 8  /* when the matrix has node blocks (B = 2 or 3 consecutive rows sharing
+                                their columns, as with B unknowns per FE node), run node-block units */
 };
 
 /* Summary of a handle (csrc_get_info). Byte counts are per product y = A x. */
@@ -100,6 +102,7 @@ typedef struct {
   int32_t tuned_rk;         /* columns per pass picked by csrc_autotune_spmm (0 = up to 8) */
   int32_t group;            /* lanes per row of the band kernel (0 before the plan is built) */
   int64_t nstages;          /* shared-memory ring stages of one single-vector product */
+  int32_t block;            /* rows per node block the single-vector product runs (1 = plain rows) */
 } csrc_info;
 
 /*

@@ -39,7 +39,7 @@ CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
 # strategies (csrc_strategy)
 CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC = 0, 1, 2, 3
 # flags
-CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH = 1, 2, 4
+CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH, CSRC_FLAG_NODE_BLOCKS = 1, 2, 4, 8
 
 STRATEGIES = {"auto": CSRC_STRAT_AUTO, "window": CSRC_STRAT_WINDOW, "color": CSRC_STRAT_COLOR,
               "atomic": CSRC_STRAT_ATOMIC}
@@ -60,6 +60,7 @@ class csrc_info(ctypes.Structure):
         ("spill_rows", ctypes.c_int64), ("accum_bytes", ctypes.c_int64), ("max_window_slots", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("tuned_strategy", ctypes.c_int32),
         ("tuned_rk", ctypes.c_int32), ("group", ctypes.c_int32), ("nstages", ctypes.c_int64),
+        ("block", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

@@ -44,6 +44,10 @@ struct csrc_matrix_s {
   bool have_rk[3] = {false, false, false};
   bool covers_rk[3] = {false, false, false};
   bool fits_rk[3] = {false, false, false};
+  int32_t block = 1;          // rows per node block found at creation (1 = none)
+  DevPlan plan_b1;            // plain-row plan when the main plan uses node blocks
+  bool have_b1 = false;
+  bool covers_b1 = false;
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -171,19 +175,25 @@ struct HostPlan {
   bool covers = true;
 };
 
-// Ring stages of band [r0, r1) for the band kernel: consecutive rows, at most `rows`
-// of them and at most `cap` pairs per stage. A row that does not fit in what is left
-// of a stage is cut there and continues in the next one. With `out` null, only counts.
-// Otherwise appends each stage's first pair and first row, then the band's end
-// (ia[r1], r1), and closes the band in band_stage. Returns the number of stages.
-int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int32_t rows, int32_t cap,
+// Ring stages of band [r0, r1) for the band kernel: consecutive units of B rows (B = 1:
+// single rows; B > 1: node blocks, which are never cut), at most `units` of them and at
+// most `cap` pairs per stage. A single row that does not fit in what is left of a stage
+// is cut there and continues in the next one. With `out` null, only counts. Otherwise
+// appends each stage's first pair and first row, then the band's end (ia[r1], r1), and
+// closes the band in band_stage. Returns the number of stages, or -1 when a node block
+// alone holds more than `cap` pairs.
+int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int32_t units, int32_t cap, int32_t B,
                      HostPlan* out) {
   int64_t k = ia[r0];
   int32_t r = r0;
   const int64_t kend = ia[r1];
   int32_t count = 0;
   while (k < kend) {
-    while (ia[(size_t)r + 1] <= k) ++r;  // the row holding pair k
+    if (B == 1) {
+      while (ia[(size_t)r + 1] <= k) ++r;  // the row holding pair k
+    } else {
+      while (ia[(size_t)r + B] <= k) r += B;  // the unit holding pair k
+    }
     const int64_t ks = k;
     if (out) {
       out->stage_k.push_back((int32_t)ks);
@@ -191,12 +201,23 @@ int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int
     }
     ++count;
     int32_t used = 0;
-    while (k < kend && used < rows) {
-      const int64_t take = std::min<int64_t>((int64_t)ia[(size_t)r + 1] - k, ks + cap - k);
+    while (k < kend && used < units) {
+      const int64_t end = ia[(size_t)r + B];
+      if (B > 1) {
+        if (end - ks > cap) {
+          if (used == 0) return -1;  // a node block larger than a stage
+          break;
+        }
+        k = end;
+        ++used;
+        r += B;
+        continue;
+      }
+      const int64_t take = std::min<int64_t>(end - k, ks + cap - k);
       if (take <= 0) break;
       k += take;
       ++used;
-      if (k < ia[(size_t)r + 1]) break;  // the row continues in the next stage
+      if (k < end) break;  // the row continues in the next stage
       ++r;
     }
   }
@@ -214,7 +235,7 @@ int32_t build_stages(const std::vector<int32_t>& ia, int32_t r0, int32_t r1, int
 // non-zero midpoint. A single row that still does not fit gets a capped window when
 // allow_overflow (targets outside it take the global-atomic path); otherwise planning fails.
 bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, int32_t budget, int mode, int rk,
-                     bool allow_overflow, int32_t stage_rows, int32_t stage_cap, HostPlan& hp) {
+                     bool allow_overflow, int32_t stage_units, int32_t stage_cap, int32_t B, HostPlan& hp) {
   const int32_t n = h->n;
   const std::vector<int32_t>& ia = h->ia;
   const std::vector<int32_t>& ja = h->ja;
@@ -254,20 +275,21 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
       }
       const int32_t phi = (r1 - 1) >> kPageShift;
       int64_t ntab = (int64_t)phi - minpage + 1;
-      const int32_t nst = build_stages(ia, r0, r1, stage_rows, stage_cap, nullptr);
+      const int32_t nst = build_stages(ia, r0, r1, stage_units, stage_cap, B, nullptr);
+      if (nst < 0) return false;
       bool fits = bytes_of((int64_t)pages.size(), ntab, r0, r1, nst) <= budget;
-      if (!fits && r1 - r0 > 1) {
+      if (!fits && r1 - r0 > B) {
         std::vector<int32_t> half;
         nnz_partition(ia, r0, r1, 2, half);
-        int32_t mid = half[1];
-        if (mid <= r0 || mid >= r1) mid = r0 + (r1 - r0) / 2;
+        int32_t mid = half[1] / B * B;  // bands hold whole node blocks
+        if (mid <= r0 || mid >= r1) mid = r0 + (r1 - r0) / (2 * B) * B;
         stack.push_back({mid, r1});  // processed after the left half
         stack.push_back({r0, mid});
         continue;
       }
       std::sort(pages.begin(), pages.end());
       if (!fits) {
-        if (!allow_overflow) return false;
+        if (!allow_overflow || B > 1) return false;
         hp.covers = false;
         // keep the band's own pages and the nearest target pages that fit
         const int64_t own = phi - (r0 >> kPageShift) + 1;
@@ -306,7 +328,7 @@ bool build_host_plan(const csrc_matrix_s* h, const std::vector<int32_t>& part, i
       }
       hp.band_wp.push_back((int32_t)hp.wpage.size());
       hp.band_row.push_back(r1);
-      build_stages(ia, r0, r1, stage_rows, stage_cap, &hp);
+      build_stages(ia, r0, r1, stage_units, stage_cap, B, &hp);
       hp.max_slots = std::max(hp.max_slots, (int32_t)pages.size() * kPageRows);
       hp.max_tab = std::max(hp.max_tab, (int32_t)ntab);
       hp.smem = std::max(hp.smem, (int32_t)used_bytes);
@@ -326,7 +348,7 @@ cudaError_t upload(T** d, const std::vector<T>& v, cudaStream_t s) {
 
 // Window plan for rk columns per pass into p (freed first). Sets covers when every
 // scatter target of every band lies in its window.
-csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, DevPlan& p, bool& covers,
+csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan& p, bool& covers,
                        std::vector<int32_t>* part_out) {
   // paper-rule partition
   int32_t nb = nbands;
@@ -339,17 +361,22 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, DevPlan& p, boo
   }
   std::vector<int32_t> part;
   nnz_partition(h->ia, 0, h->n, nb, part);
+  // execution bands start at node-block boundaries
+  std::vector<int32_t> epart(part);
+  if (B > 1)
+    for (auto& v : epart) v = v == h->n ? v : v / B * B;
   const int mode = mode_of(h->arith, h->storage);
   const int32_t budget = band_smem_limit(mode) - band_ring_bytes(mode);  // everything after the ring
-  // lanes per row: the smallest G whose T/G rows of average length fill at most one stage
-  const double avg = h->n > 0 ? (double)h->h / (double)h->n : 0.0;
+  // lanes per unit: the smallest G whose T/G units of average size fill at most one stage
+  const double avg = h->n > 0 ? (double)B * (double)h->h / (double)h->n : 0.0;
   int32_t group = 1;
-  while (group < 8 && (double)(kBandThreads / group) * avg > (double)kStageCap) group *= 2;
+  const int32_t gmax = B > 1 ? 16 : 8;
+  while (group < gmax && (double)(kBandThreads / group) * avg > (double)kStageCap) group *= 2;
   HostPlan hp;
-  bool ok = build_host_plan(h, part, budget, mode, rk, false, kBandThreads / group, kStageCap, hp);
-  if (!ok && rk == 1) {
+  bool ok = build_host_plan(h, epart, budget, mode, rk, false, kBandThreads / group, kStageCap, B, hp);
+  if (!ok && rk == 1 && B == 1) {
     hp = HostPlan();
-    ok = build_host_plan(h, part, budget, mode, rk, true, kBandThreads / group, kStageCap, hp);
+    ok = build_host_plan(h, epart, budget, mode, rk, true, kBandThreads / group, kStageCap, B, hp);
   }
   if (!ok) return CSRC_ERR_NOT_PARTITIONED;
   // accumulation map: group spill entries by row (stable: band order)
@@ -406,6 +433,7 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, DevPlan& p, boo
   CSRC_TRY(cudaStreamSynchronize(s));
   p.spill = hp.spill;
   p.group = group;
+  p.block = B;
   p.nstages = (int64_t)hp.stage_k.size() - kMetaPad - (int64_t)(hp.band_stage.size() - 1);
   p.nacc = (int64_t)acc_row.size();
   p.max_slots = hp.max_slots;
@@ -428,10 +456,36 @@ csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
     h->have_rk[i] = false;
   }
   h->have_plan = false;
-  CSRC_TRY_S(build_plan(h, nbands, 1, h->plan, h->plan_covers, &h->part));
+  free_plan(h->plan_b1);
+  h->have_b1 = false;
+  csrc_status st = CSRC_ERR_NOT_PARTITIONED;
+  if (h->block > 1) {
+    st = build_plan(h, nbands, 1, h->block, h->plan, h->plan_covers, &h->part);
+    if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
+    if (st == CSRC_OK && !h->plan_covers) st = CSRC_ERR_NOT_PARTITIONED;
+  }
+  if (st != CSRC_OK) CSRC_TRY_S(build_plan(h, nbands, 1, 1, h->plan, h->plan_covers, &h->part));
   h->part_nbands = nbands;
   h->have_plan = true;
   ++h->generation;
+  return CSRC_OK;
+}
+
+// A single-vector plan of plain rows (the atomic strategy and the batched kernel run
+// rows one at a time): the main plan, or, when that one uses node blocks, a second plan.
+csrc_status plan_b1_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
+  if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
+  if (h->plan.block == 1) {
+    *out = &h->plan;
+    *covers = h->plan_covers;
+    return CSRC_OK;
+  }
+  if (!h->have_b1) {
+    CSRC_TRY_S(build_plan(h, h->part_nbands, 1, 1, h->plan_b1, h->covers_b1, nullptr));
+    h->have_b1 = true;
+  }
+  *out = &h->plan_b1;
+  *covers = h->covers_b1;
   return CSRC_OK;
 }
 
@@ -445,7 +499,7 @@ csrc_status plan_for(csrc_matrix_s* h, int rk, DevPlan** out, bool* covers) {
   }
   const int i = rk == 2 ? 0 : (rk == 4 ? 1 : 2);
   if (!h->have_rk[i]) {
-    const csrc_status st = build_plan(h, h->part_nbands, rk, h->plan_rk[i], h->covers_rk[i], nullptr);
+    const csrc_status st = build_plan(h, h->part_nbands, rk, 1, h->plan_rk[i], h->covers_rk[i], nullptr);
     if (st == CSRC_ERR_NOT_PARTITIONED) {
       h->have_rk[i] = true;  // remembered: no window of rk columns fits this matrix
       h->fits_rk[i] = false;
@@ -544,6 +598,7 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
   a.x_bulk = (reinterpret_cast<uintptr_t>(x) & 15u) == 0u;
   a.ldx = ldx;
   a.rk = rk;
+  a.block = p.block;
   return a;
 }
 
@@ -589,15 +644,18 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
       }));
     }
   } else {
-    const BandArgs a = band_args(h, h->plan, transpose, dx, dy, h->plan.spill_buf, 1, 1);
     const bool atomic = strat == CSRC_STRAT_ATOMIC;
+    DevPlan* p = &h->plan;  // the atomic strategy runs plain rows
+    bool covers = h->plan_covers;
+    if (atomic) CSRC_TRY_S(plan_b1_for(h, &p, &covers));
+    const BandArgs a = band_args(h, *p, transpose, dx, dy, p->spill_buf, 1, 1);
     if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
-                          [&] { return launch_band(h->arith, h->storage, atomic, a, h->plan.nb, h->plan.smem_bytes, s); }));
-    if (!atomic && h->plan.nacc > 0)
+                          [&] { return launch_band(h->arith, h->storage, atomic, a, p->nb, p->smem_bytes, s); }));
+    if (!atomic && p->nacc > 0)
       CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
-        return launch_accumulate(h->arith, h->storage, h->plan.nacc, 1, 1, h->plan.acc_row, h->plan.acc_ptr,
-                                 h->plan.acc_src, h->plan.spill_buf, dy, s);
+        return launch_accumulate(h->arith, h->storage, p->nacc, 1, 1, p->acc_row, p->acc_ptr, p->acc_src,
+                                 p->spill_buf, dy, s);
       }));
   }
   if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, s));
@@ -737,7 +795,7 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
     if (xa < ya + vb && ya < xa + vb) return fail(CSRC_ERR_ALIAS);
     DevPlan* p = nullptr;
     bool covers = false;
-    csrc_status st = plan_for(h, 1, &p, &covers);
+    csrc_status st = plan_b1_for(h, &p, &covers);  // the batched kernel runs plain rows
     if (st != CSRC_OK) return fail(st);
     e->gens.push_back(h->generation);
     const bool atomic = h->tuned == CSRC_STRAT_ATOMIC || !covers;
@@ -838,6 +896,37 @@ csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X
                                 e->kernels));
 }
 
+// Rows per node block: the largest B in {3, 2} such that n is a multiple of B and every
+// unit of rows r = qB .. qB+B-1 has the node-block shape the band kernel exploits: row
+// r+t holds row r's columns (all below r, same order) followed by columns r .. r+t-1.
+// FE matrices with B unknowns per node interleaved (B-by-B dense node blocks) have it.
+// Returns 1 when neither size fits.
+int32_t detect_node_blocks(int32_t n, const std::vector<int32_t>& ia, const std::vector<int32_t>& ja) {
+  for (int32_t B = 3; B >= 2; --B) {
+    if (n < B || n % B != 0) continue;
+    bool ok = true;
+    for (int32_t r = 0; r < n && ok; r += B) {
+      const int32_t L0 = ia[(size_t)r + 1] - ia[(size_t)r];
+      for (int32_t t = 1; t < B && ok; ++t) {
+        const int32_t kb = ia[(size_t)r + t];
+        if (ia[(size_t)r + t + 1] - kb != L0 + t) {
+          ok = false;
+          break;
+        }
+        for (int32_t m = 0; m < L0; ++m)
+          if (ja[(size_t)kb + m] != ja[(size_t)ia[(size_t)r] + m]) {
+            ok = false;
+            break;
+          }
+        for (int32_t q = 0; q < t && ok; ++q)
+          if (ja[(size_t)kb + L0 + q] != r + q) ok = false;
+      }
+    }
+    if (ok) return B;
+  }
+  return 1;
+}
+
 csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
                                  const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream) {
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
@@ -912,6 +1001,7 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   m->h = h64;
   m->storage = storage;
   m->flags = flags;
+  m->block = (flags & CSRC_FLAG_NODE_BLOCKS) ? detect_node_blocks(n, ia, ja) : 1;
   cudaGetDevice(&m->device);
   cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   if (m->sms <= 0) m->sms = 1;
@@ -1034,7 +1124,8 @@ csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row
   *out = nullptr;
   if (n < 0 || !row_ptr) return CSRC_ERR_INVALID_ARG;
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
-  if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH))
+  if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
+                         CSRC_FLAG_NODE_BLOCKS))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1380,6 +1471,7 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   info->tuned_strategy = h->tuned;
   info->tuned_rk = h->tuned_rk;
   info->group = h->have_plan ? h->plan.group : 0;
+  info->block = h->have_plan ? h->plan.block : h->block;
   info->nstages = h->have_plan ? h->plan.nstages : 0;
   return CSRC_OK;
 }
@@ -1404,6 +1496,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   cudaDeviceSynchronize();
   free_plan(h->plan);
   for (int i = 0; i < 3; ++i) free_plan(h->plan_rk[i]);
+  free_plan(h->plan_b1);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);

@@ -37,6 +37,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "df32.cuh"
 #include "internal.h"
@@ -197,11 +198,121 @@ struct RowX<MODE_DF> {
 
 
 // ---------------------------------------------------------------------------- the band kernel
+// One unit of B consecutive rows r .. r+B-1 of a node block (B degrees of freedom per
+// node, dense B-by-B node blocks): row r+t holds the L0 pairs of row r's columns (all
+// below r), in the same order, then t pairs for columns r .. r+t-1. The host checked that
+// structure for every unit of the matrix. A group of G lanes takes the unit: per shared
+// column it looks up the window slot and loads x once, gathers into the B row sums, and
+// scatters the sum of the B products with one window update. The unit's pairs are whole
+// in the ring stage (s* point at the stage, indexed by pair number).
+template <int MODE, int G, int B>
+__device__ __forceinline__ void block_unit(int r, const int32_t* s_ia, const int32_t* sja,
+                                           const typename Traits<MODE>::V* sal, const typename Traits<MODE>::V* sau,
+                                           Window<MODE>& win, const int32_t* tab, int plo, int ntab, int gl,
+                                           unsigned gmask, unsigned& bad) {
+  using V = typename Traits<MODE>::V;
+  using X = typename Traits<MODE>::X;
+  using XR = typename RowX<MODE>::type;
+  auto lookup = [&](int j) -> int {
+    const int t = (j >> kPageShift) - plo;
+    const int pb = (unsigned)t < (unsigned)ntab ? tab[t] : -1;
+    bad |= pb < 0 ? 4u : 0u;
+    return max(pb, 0) + (j & (kPageRows - 1));
+  };
+  int kbt[B], rs[B];
+  XR xr[B];
+  X acc[B];
+#pragma unroll
+  for (int t = 0; t < B; ++t) {
+    kbt[t] = s_ia[r + t];
+    rs[t] = lookup(r + t);
+    if constexpr (MODE == MODE_DF) {
+      xr[t] = df_split<true>(win.xs[rs[t]], &bad);
+    } else {
+      xr[t] = win.xs[rs[t]];
+    }
+    acc[t] = X(0);
+  }
+  const int L0 = s_ia[r + 1] - kbt[0];
+  // shared columns
+  for (int m = gl; m < L0; m += G) {
+    const int sv = lookup(sja[kbt[0] + m]);
+    const X xj = win.xs[sv];
+    if constexpr (MODE == MODE_DF) {
+      df32 p;
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        acc[t] = fma(sal[kbt[t] + m], xj, acc[t]);
+        const df32 q = df_mul(df_split<false>(sau[kbt[t] + m], nullptr), xr[t]);
+        if (t == 0) p = q; else df_acc(p, q);
+      }
+      df_atomic_add(win.whi + sv, win.wlo + sv, p);
+    } else if constexpr (MODE == MODE_F64) {
+      double p = 0.0;
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        acc[t] = fma(sal[kbt[t] + m], xj, acc[t]);
+        p = fma(sau[kbt[t] + m], xr[t], p);
+      }
+      atomicAdd(win.w + sv, p);
+    } else {
+      float p = 0.f;
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        acc[t] = __fmaf_rn(as_f32<MODE>(sal[kbt[t] + m]), xj, acc[t]);
+        p = __fmaf_rn(as_f32<MODE>(sau[kbt[t] + m]), xr[t], p);
+      }
+      atomicAdd(win.w + sv, p);
+    }
+  }
+  // the unit's own block: pair q of row r+t's tail couples rows r+t and r+q (q < t)
+#pragma unroll
+  for (int t = 1; t < B; ++t) {
+#pragma unroll
+    for (int q = 0; q < t; ++q) {
+      if (gl == ((t * (t - 1) / 2 + q) % G)) {
+        const int k = kbt[t] + L0 + q;
+        const int sv = lookup(sja[k]);
+        if constexpr (MODE == MODE_DF) {
+          acc[t] = fma(sal[k], win.xs[sv], acc[t]);
+          df_atomic_add(win.whi + sv, win.wlo + sv, df_mul(df_split<false>(sau[k], nullptr), xr[t]));
+        } else if constexpr (MODE == MODE_F64) {
+          acc[t] = fma(sal[k], win.xs[sv], acc[t]);
+          atomicAdd(win.w + sv, sau[k] * xr[t]);
+        } else {
+          acc[t] = __fmaf_rn(as_f32<MODE>(sal[k]), win.xs[sv], acc[t]);
+          atomicAdd(win.w + sv, __fmul_rn(as_f32<MODE>(sau[k]), xr[t]));
+        }
+      }
+    }
+  }
+  // the B row sums, reduced across the group and added once each
+#pragma unroll
+  for (int t = 0; t < B; ++t) {
+    if constexpr (MODE == MODE_DF) {
+      df32 v = df_split<false>(acc[t], nullptr);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        df32 u;
+        u.hi = __shfl_xor_sync(gmask, v.hi, o, G);
+        u.lo = __shfl_xor_sync(gmask, v.lo, o, G);
+        df_acc(v, u);
+      }
+      if (gl == 0) df_atomic_add(win.whi + rs[t], win.wlo + rs[t], v);
+    } else {
+      X v = acc[t];
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, G);
+      if (gl == 0) atomicAdd(win.w + rs[t], v);
+    }
+  }
+}
+
 // One band b of the product described by a, run by the whole CTA. The CTA may run
 // several bands one after another (the batched kernel): its mbarriers are initialised at
 // the start and invalidated at the end. Returns false when a bounded wait ran out (the
 // status word says so and the CTA must not run further bands).
-template <int MODE, int G, bool ATOMIC, int RK>
+template <int MODE, int G, bool ATOMIC, int RK, int B = 1>
 __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   using Sh = BandShape<MODE>;
   using V = typename Traits<MODE>::V;
@@ -213,6 +324,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   constexpr int VB = (int)sizeof(V);
   constexpr int XB = (int)sizeof(X);
   static_assert(!ATOMIC || RK == 1, "the atomic strategy runs single vectors");
+  static_assert(B == 1 || (RK == 1 && !ATOMIC), "row blocks run single vectors with the window strategy");
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int tid = threadIdx.x;
@@ -356,7 +468,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
     const uint32_t parity = (uint32_t)((s / NS) & 1);
     const int ks = s_sk[st0 + s];
     const int ke = s_sk[st0 + s + 1];
-    const int r = s_sr[st0 + s] + rowoff;
+    const int r = s_sr[st0 + s] + rowoff * B;  // first row of this group's unit (B rows)
     int kb = 0, kx = 0;  // this group's pairs [kb, kx) of row r inside the stage
     if (r < r1) {
       kb = max(s_ia[r], ks);
@@ -366,7 +478,13 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
       timed_out = true;
       break;
     }
-    if (kb < kx) {  // the whole group enters (its lanes meet in the shuffles below)
+    if constexpr (B > 1) {
+      // stages hold whole units: this group's unit is in stage s when it starts before its end
+      if (r < r1 && s_ia[r] < ke) block_unit<MODE, G, B>(r, s_ia, ring_ja + (size_t)slot * SP - (ks & ~(kPairAlign - 1)),
+                                         ring_al + (size_t)slot * SP - (ks & ~(kPairAlign - 1)),
+                                         ring_au + (size_t)slot * SP - (ks & ~(kPairAlign - 1)), win, tab, plo,
+                                         ntab, gl, gmask, bad);
+    } else if (kb < kx) {  // the whole group enters (its lanes meet in the shuffles below)
       const int base = ks & ~(kPairAlign - 1);
       const int32_t* sja = ring_ja + (size_t)slot * SP - base;
       const V* sal = ring_al + (size_t)slot * SP - base;
@@ -417,28 +535,35 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
           for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < RK; ++c) xv[u][c] = win.xs[sv[u] * RK + c];
+          if constexpr (MODE == MODE_DF) {
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            if (k0 + u * G < kx) {
-              if constexpr (MODE == MODE_DF) {
+            for (int u = 0; u < U; ++u) {
+              if (k0 + u * G < kx) {
                 const df32 vs = df_split<false>(vv[u], nullptr);
 #pragma unroll
                 for (int c = 0; c < RK; ++c) {
                   acc[c] = fma(gv[u], xv[u][c], acc[c]);
                   df_atomic_add(win.whi + sv[u] * RK + c, win.wlo + sv[u] * RK + c, df_mul(vs, xr[c]));
                 }
-              } else if constexpr (MODE == MODE_F64) {
+              }
+            }
+          } else {
 #pragma unroll
-                for (int c = 0; c < RK; ++c) {
-                  acc[c] = fma(gv[u], xv[u][c], acc[c]);
-                  atomicAdd(win.w + sv[u] * RK + c, vv[u] * xr[c]);
-                }
-              } else {
-                const float g32 = as_f32<MODE>(gv[u]), v32 = as_f32<MODE>(vv[u]);
+            for (int u = 0; u < U; ++u) {
+              if (k0 + u * G < kx) {
+                if constexpr (MODE == MODE_F64) {
 #pragma unroll
-                for (int c = 0; c < RK; ++c) {
-                  acc[c] = __fmaf_rn(g32, xv[u][c], acc[c]);
-                  atomicAdd(win.w + sv[u] * RK + c, __fmul_rn(v32, xr[c]));
+                  for (int c = 0; c < RK; ++c) {
+                    acc[c] = fma(gv[u], xv[u][c], acc[c]);
+                    atomicAdd(win.w + sv[u] * RK + c, vv[u] * xr[c]);
+                  }
+                } else {
+                  const float g32 = as_f32<MODE>(gv[u]), v32 = as_f32<MODE>(vv[u]);
+#pragma unroll
+                  for (int c = 0; c < RK; ++c) {
+                    acc[c] = __fmaf_rn(g32, xv[u][c], acc[c]);
+                    atomicAdd(win.w + sv[u] * RK + c, __fmul_rn(v32, xr[c]));
+                  }
                 }
               }
             }
@@ -581,15 +706,15 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   return true;
 }
 
-template <int MODE, int G, bool ATOMIC, int RK>
+template <int MODE, int G, bool ATOMIC, int RK, int B = 1>
 __global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
-  band_body<MODE, G, ATOMIC, RK>(a, blockIdx.x + a.band_offset);
+  band_body<MODE, G, ATOMIC, RK, B>(a, blockIdx.x + a.band_offset);
 }
 
 // Dynamic shared memory limit of one instantiation.
-template <int MODE, int G, bool ATOMIC, int RK>
+template <int MODE, int G, bool ATOMIC, int RK, int B = 1>
 cudaError_t set_band_smem() {
-  return cudaFuncSetAttribute(band_kernel<MODE, G, ATOMIC, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(band_kernel<MODE, G, ATOMIC, RK, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               band_smem_limit(MODE));
 }
 

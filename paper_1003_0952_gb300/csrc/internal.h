@@ -112,7 +112,8 @@ inline int mode_of(Arith arith, int storage) {
 // indexed through a page table that spans pages [band_plo[b], band_plo[b] + band_ntab[b]).
 struct DevPlan {
   int32_t nb = 0;
-  int32_t group = 1;             // lanes per row (1, 2, 4 or 8)
+  int32_t group = 1;             // lanes per row unit (1, 2, 4, 8 or 16)
+  int32_t block = 1;             // rows per unit: node blocks of 2 or 3 rows, else 1
   int64_t nstages = 0;           // ring stages over all bands
   int32_t* band_stage = nullptr; // nb+1: stages of band b are [band_stage[b], band_stage[b+1]-1)
   int32_t* stage_k = nullptr;    // first pair of each stage (the band's last entry is its end)
@@ -150,6 +151,7 @@ struct BandArgs {
   int32_t x_bulk; // x is 16-byte aligned: window pages of x are fetched with bulk copies
   int32_t ldx;    // row stride of x and y in elements (1 for a single vector)
   int32_t rk;     // columns per pass (1, 2, 4 or 8); x and y point at the pass's first column
+  int32_t block;  // rows per unit (node blocks), 1 for plain rows
   const void* al;  // gathered values  (au for the transpose)
   const void* au;  // scattered values (al for the transpose)
   const void* ad;
@@ -188,6 +190,8 @@ cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, in
                               cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
+cudaError_t prepare_band_kernels_block();
+cudaError_t launch_band_block(Arith arith, int storage, const BandArgs& a, int nbands, int smem, cudaStream_t s);
 
 // Batched products (batch.cu).
 cudaError_t prepare_batch_kernels();

@@ -44,6 +44,7 @@ cudaError_t prepare_band_kernels() {
   if ((r = set_smem_mode<MODE_F32>()) != cudaSuccess) e = r;
   if ((r = set_smem_mode<MODE_BF16>()) != cudaSuccess) e = r;
   if ((r = prepare_band_kernels_rk()) != cudaSuccess) e = r;
+  if ((r = prepare_band_kernels_block()) != cudaSuccess) e = r;
   return e;
 }
 
@@ -66,6 +67,7 @@ cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandA
                         cudaStream_t s) {
   if (nbands <= 0) return cudaSuccess;
   if (a.rk > 1) return launch_band_rk(arith, storage, a, nbands, smem, s);
+  if (a.block > 1) return launch_band_block(arith, storage, a, nbands, smem, s);
   const int mode = mode_of(arith, storage);
   dim3 grid(nbands);
   switch (mode) {

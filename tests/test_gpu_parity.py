@@ -383,3 +383,46 @@ def test_autotune_picks_a_strategy_and_stays_correct(cs):
             _check(m, x, h.run(x, "auto", tr), tr, TOL["f64"])
     finally:
         h.close()
+
+
+# --------------------------------------------------------------------------- node blocks
+@pytest.mark.parametrize("ndof", [2, 3])
+def test_node_block_kernel_matches_plain_rows_and_oracle(cs, ndof):
+    # with CSRC_FLAG_NODE_BLOCKS, matrices with ndof unknowns per node run node-block
+    # units; they, the plain-row kernel and the oracle must agree
+    m = fe.q1_hex(10, ndof, 51)
+    im = fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 52))
+    xi = fe.integer_vector(m.n, 53)
+    x = fe.source_vector(m.n, 54)
+    for storage in ("f64", "f32", "bf16"):
+        hb = Handle(cs, im, storage, flags=cs.CSRC_FLAG_NODE_BLOCKS)
+        hp = Handle(cs, im, storage)
+        try:
+            for tr in (False, True):
+                yb = hb.run(xi, "window", tr)
+                np.testing.assert_array_equal(yb, _ref(im, xi, tr))
+                np.testing.assert_array_equal(hp.run(xi, "window", tr), yb)
+            assert cs.csrc_get_info(hb.h)["block"] == ndof
+            assert cs.csrc_get_info(hp.h)["block"] == 1
+        finally:
+            hb.close()
+            hp.close()
+    h = Handle(cs, m, flags=cs.CSRC_FLAG_NODE_BLOCKS)
+    try:
+        for nb in (1, 5, 152):
+            for tr in (False, True):
+                _check(m, x, h.run(x, "window", tr, nbands=nb), tr, TOL["f64"])
+        # the atomic strategy runs plain rows on a second plan
+        _check(m, x, h.run(x, "atomic"), False, TOL["f64"])
+    finally:
+        h.close()
+
+
+def test_scalar_matrix_has_no_node_blocks(cs):
+    m = fe.q1_hex(8, 1, 3)
+    h = Handle(cs, m)
+    try:
+        h.run(fe.source_vector(m.n, 4))
+        assert cs.csrc_get_info(h.h)["block"] == 1
+    finally:
+        h.close()
