@@ -1,0 +1,138 @@
+"""Parity at the full sizes of the benchmark configurations, in the launch configuration
+the benchmark times (window strategy, automatic partition), against the CPU oracle.
+
+Every product is compared in full (the oracle's Fig. 2(a) product in plain C takes well
+under a second per product at these sizes). The tolerances are the stated ones, relative
+to sum_j |a_ij||x_j| per row: 1e-12 (FP64 storage), 1e-5 (FP32), 1e-2 (BF16). Each test
+prints the measured maximum, which the design notes quote.
+"""
+import numpy as np
+import pytest
+
+import fe_inputs as fe
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def cs():
+    from paper_1003_0952_gb300 import build
+
+    build.build()
+    import paper_1003_0952_gb300 as m
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return m
+
+
+def _product(cs, h, x, storage, strategy, transpose):
+    dt = torch.float64 if storage == "f64" else torch.float32
+    xd = torch.as_tensor(x, dtype=dt).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    (cs.csrc_spmv_t if transpose else cs.csrc_spmv)(h, xd, yd, cs.STRATEGIES[strategy], torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert cs.csrc_get_last_device_error(h) == cs.CSRC_OK
+    return yd.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["q1s_96", "q1v_96"])
+def test_q1_fp64_all_strategies(cs, name):
+    builder, xseed = fe.CONFIGS[name]
+    m = builder()
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, xseed)
+    refs = {False: oracle.csrc_spmv(c, x), True: oracle.csrc_spmv_t(c, x)}
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        cs.csrc_partition(h, 0)
+        cs.csrc_color(h, 12345)
+        for strategy in ("window", "atomic", "color"):
+            for tr in (False, True):
+                err = oracle.max_rel_err(m, x, _product(cs, h, x, "f64", strategy, tr), refs[tr], transpose=tr)
+                print(f"{name} f64 {strategy} transpose={tr}: max rel err {err:.3e}")
+                assert err <= TOL["f64"], (strategy, tr, err)
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_tet_2m_reduced_precision(cs):
+    # 2M-node tetrahedral mesh (Kuhn lattice, 14 neighbours per interior node, RCM order)
+    m = fe.tet_mesh(2_000_000, 1003, method="kuhn")
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, 2003).astype(np.float32).astype(np.float64)
+    y_ref = oracle.csrc_spmv(c, x)
+    for storage in ("f64", "f32", "bf16"):
+        h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+        try:
+            err = oracle.max_rel_err(m, x, _product(cs, h, x, storage, "window", False), y_ref)
+            print(f"tet_kuhn_2m {storage}: max rel err {err:.3e}")
+            assert err <= TOL[storage], (storage, err)
+        finally:
+            cs.csrc_destroy(h)
+
+
+def test_delaunay_tets_reduced_precision(cs):
+    # an irregular (Delaunay) tetrahedral pattern at a size the host generates quickly
+    m = fe.tet_mesh(200_000, 1003, method="delaunay")
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, 2003).astype(np.float32).astype(np.float64)
+    refs = {False: oracle.csrc_spmv(c, x), True: oracle.csrc_spmv_t(c, x)}
+    for storage in ("f64", "f32"):
+        h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+        try:
+            for tr in (False, True):
+                err = oracle.max_rel_err(m, x, _product(cs, h, x, storage, "window", tr), refs[tr], transpose=tr)
+                print(f"tet_delaunay_200k {storage} transpose={tr}: max rel err {err:.3e}")
+                assert err <= TOL[storage]
+        finally:
+            cs.csrc_destroy(h)
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+def test_q1s_several_right_hand_sides(cs, storage):
+    builder, _ = fe.CONFIGS["q1s_96"]
+    m = builder()
+    c = oracle.from_matrix(m)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+    dt = torch.float64 if storage == "f64" else torch.float32
+    try:
+        for r in (4, 8, 16, 32):
+            X = fe.source_vector(m.n, 2004, nrhs=r)
+            if storage != "f64":
+                X = X.astype(np.float32).astype(np.float64)
+            Xd = torch.as_tensor(X, dtype=dt).cuda()
+            Yd = torch.full_like(Xd, float("nan"))
+            cs.csrc_autotune_spmm(h, Xd, Yd, r, torch.cuda.current_stream())
+            Yd.fill_(float("nan"))
+            cs.csrc_spmm_batched([h], [Xd], [Yd], r, False, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            err = oracle.max_rel_err(m, X, Yd.cpu().numpy().astype(np.float64), oracle.csrc_spmm(c, X))
+            print(f"q1s_96 {storage} nrhs={r} k_tile={cs.csrc_get_info(h)['tuned_rk']}: max rel err {err:.3e}")
+            assert err <= TOL[storage], (r, err)
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_batch_256_graph(cs):
+    ms = fe.batch_meshes(256, 1005)
+    hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F32) for m in ms]
+    try:
+        xs = [fe.source_vector(m.n, 9 + i).astype(np.float32).astype(np.float64) for i, m in enumerate(ms)]
+        Xd = [torch.as_tensor(x, dtype=torch.float32).cuda() for x in xs]
+        Yd = [torch.full_like(x, float("nan")) for x in Xd]
+        cs.csrc_spmm_batched(hs, Xd, Yd, 1, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        worst = 0.0
+        for m, x, y in zip(ms, xs, Yd):
+            err = oracle.max_rel_err(m, x, y.cpu().numpy().astype(np.float64), oracle.csrc_spmv(oracle.from_matrix(m), x))
+            worst = max(worst, err)
+        print(f"batch_256 f32 graph: max rel err over all members {worst:.3e}")
+        assert worst <= TOL["f32"]
+    finally:
+        for h in hs:
+            cs.csrc_destroy(h)

@@ -346,28 +346,6 @@ def test_coo_and_padding(cs):
         cs.csrc_destroy(h)
 
 
-# --------------------------------------------------------------------------- full-size configurations
-@pytest.mark.slow
-@pytest.mark.parametrize("name", ["q1s_96", "q1v_96"])
-def test_full_size_q1(cs, name):
-    builder, xseed = fe.CONFIGS[name]
-    m = builder()
-    x = fe.source_vector(m.n, xseed)
-    yref = oracle.csr_spmv(m.n, m.row_ptr, m.col, m.val, x)
-    mt = _transpose(m) if name == "q1s_96" else None
-    h = Handle(cs, m)
-    try:
-        for strategy in ("window", "atomic"):
-            y = h.run(x, strategy)
-            err = oracle.max_rel_err(m, x, y, yref)
-            assert err <= TOL["f64"], (strategy, err)
-        if mt is not None:
-            y = h.run(x, "window", True)
-            assert oracle.max_rel_err(mt, x, y, oracle.csr_spmv(m.n, mt.row_ptr, mt.col, mt.val, x)) <= TOL["f64"]
-    finally:
-        h.close()
-
-
 # --------------------------------------------------------------------------- autotuner
 def test_autotune_picks_a_strategy_and_stays_correct(cs):
     m = fe.q1_hex(16, 3, 44)
