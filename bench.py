@@ -41,7 +41,7 @@ if ROOT not in sys.path:
 
 METRIC = "CSRC SpMV GB/s and % of HBM roofline (FP64 vs mixed-prec batched, 1 GB300)"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["kernels.cu", "df32.cuh", "internal.h"]
+KERNEL_SOURCES = ["kernels.cu", "band.cuh", "df32.cuh", "internal.h"]
 
 
 # ----------------------------------------------------------------------------- helpers

@@ -372,11 +372,15 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
   int32_t group = 1;
   const int32_t gmax = B > 1 ? 16 : 8;
   while (group < gmax && (double)(kBandThreads / group) * avg > (double)kStageCap) group *= 2;
+  // long single-vector rows (32 or more pairs on average): 16 lanes per row in a CTA of
+  // twice the threads; a stage still holds 64 rows
+  if (B == 1 && rk == 1 && group == 8 && avg >= 32.0) group = 16;
+  const int32_t units = band_threads(group, B, rk) / group;
   HostPlan hp;
-  bool ok = build_host_plan(h, epart, budget, mode, rk, false, kBandThreads / group, kStageCap, B, hp);
+  bool ok = build_host_plan(h, epart, budget, mode, rk, false, units, kStageCap, B, hp);
   if (!ok && rk == 1 && B == 1) {
     hp = HostPlan();
-    ok = build_host_plan(h, epart, budget, mode, rk, true, kBandThreads / group, kStageCap, B, hp);
+    ok = build_host_plan(h, epart, budget, mode, rk, true, units, kStageCap, B, hp);
   }
   if (!ok) return CSRC_ERR_NOT_PARTITIONED;
   // accumulation map: group spill entries by row (stable: band order)
@@ -800,6 +804,8 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
     e->gens.push_back(h->generation);
     const bool atomic = h->tuned == CSRC_STRAT_ATOMIC || !covers;
     members[(size_t)b] = band_args(h, *p, transpose != 0, X[b], Y[b], p->spill_buf, 1, 1);
+    // plans with 16 lanes per row run with 8 in the 512-thread batched kernel (64 groups:
+    // a stage holds at most 64 rows either way)
     const int lg = p->group == 1 ? 0 : (p->group == 2 ? 1 : (p->group == 4 ? 2 : 3));
     for (int32_t band = 0; band < p->nb; ++band)
       groups[lg][atomic ? 1 : 0].push_back({b, band, p->band_pairs[(size_t)band]});

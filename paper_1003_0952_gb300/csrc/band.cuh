@@ -318,7 +318,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   using V = typename Traits<MODE>::V;
   using X = typename Traits<MODE>::X;
   using XR = typename RowX<MODE>::type;
-  constexpr int T = Sh::T;
+  constexpr int T = band_threads(G, B, RK);
   constexpr int NS = Sh::NS;
   constexpr int SP = Sh::kSlotPairs;  // pairs per ring slot
   constexpr int VB = (int)sizeof(V);
@@ -511,7 +511,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
         // slot lookup needs no branch (a page missing from the table would be a plan error:
         // it is flagged, and its value goes to an in-range slot). U pairs per lane are
         // loaded before any of them is scattered, so their shared-memory latencies overlap.
-        constexpr int U = RK >= 4 ? 1 : 4 / RK;
+        constexpr int U = RK >= 4 ? 1 : (RK == 1 && G == 16 ? 3 : 4 / RK);
         for (int k0 = kb + gl; k0 < kx; k0 += U * G) {
           int jv[U], sv[U];
           V gv[U], vv[U];
@@ -707,7 +707,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
 }
 
 template <int MODE, int G, bool ATOMIC, int RK, int B = 1>
-__global__ void __launch_bounds__(BandShape<MODE>::T, BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
+__global__ void __launch_bounds__(band_threads(G, B, RK), BandShape<MODE>::kCtasPerSm) band_kernel(BandArgs a) {
   band_body<MODE, G, ATOMIC, RK, B>(a, blockIdx.x + a.band_offset);
 }
 

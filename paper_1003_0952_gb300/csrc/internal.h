@@ -37,6 +37,12 @@ struct BandShape {
   static constexpr int ring_bytes() { return NS * kSlotPairs * (4 + 2 * kValueBytes); }
 };
 constexpr int kBandThreads = 512;
+// Threads of a band CTA: 512, or 1024 when single-vector rows are taken by 16 lanes each
+// (rows of 32 or more pairs): twice the warps hide more shared-memory latency, and the
+// kernel then fits in 64 registers per thread.
+__host__ __device__ constexpr int band_threads(int G, int B, int RK) {
+  return (G == 16 && B == 1 && RK == 1) ? 1024 : kBandThreads;
+}
 constexpr int kStageCap = 2560;
 
 // Shared memory ahead of the ring (mbarriers: NS full, NS empty, one for the band's set-up copies).

@@ -34,6 +34,8 @@ static cudaError_t set_smem_mode() {
   if ((r = set_band_smem<MODE, 4, true, 1>()) != cudaSuccess) e = r;
   if ((r = set_band_smem<MODE, 8, false, 1>()) != cudaSuccess) e = r;
   if ((r = set_band_smem<MODE, 8, true, 1>()) != cudaSuccess) e = r;
+  if ((r = set_band_smem<MODE, 16, false, 1>()) != cudaSuccess) e = r;
+  if ((r = set_band_smem<MODE, 16, true, 1>()) != cudaSuccess) e = r;
   return e;
 }
 
@@ -50,15 +52,15 @@ cudaError_t prepare_band_kernels() {
 
 template <int MODE>
 static void launch_mode(int group, bool atomic, const BandArgs& a, dim3 grid, int smem, cudaStream_t s) {
-  constexpr int T = BandShape<MODE>::T;
-#define CSRC_G(GV)                                                           \
-  if (atomic) band_kernel<MODE, GV, true, 1><<<grid, T, smem, s>>>(a);       \
-  else band_kernel<MODE, GV, false, 1><<<grid, T, smem, s>>>(a);
+#define CSRC_G(GV)                                                                        \
+  if (atomic) band_kernel<MODE, GV, true, 1><<<grid, band_threads(GV, 1, 1), smem, s>>>(a); \
+  else band_kernel<MODE, GV, false, 1><<<grid, band_threads(GV, 1, 1), smem, s>>>(a);
   switch (group) {
     case 1: CSRC_G(1) break;
     case 2: CSRC_G(2) break;
     case 4: CSRC_G(4) break;
-    default: CSRC_G(8) break;
+    case 8: CSRC_G(8) break;
+    default: CSRC_G(16) break;
   }
 #undef CSRC_G
 }

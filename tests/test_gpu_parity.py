@@ -200,6 +200,31 @@ def test_mixed_precision_error(cs, storage, strategy):
         h.close()
 
 
+# --------------------------------------------------------------------------- long rows: 16 lanes per row
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_long_rows_run_sixteen_lanes(cs, storage):
+    # 3 DOF per node on a 14^3 grid: about 34 pairs per row, taken by 16 lanes in a
+    # 1024-thread CTA (three pairs per lane per pass, so rows of up to 48 pairs in one pass)
+    m = fe.q1_hex(14, 3, 23)
+    x = fe.source_vector(m.n, 24)
+    if storage != "f64":
+        x = x.astype(np.float32).astype(np.float64)
+    mi = fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 25))
+    xi = fe.integer_vector(m.n, 26)
+    h, hi = Handle(cs, m, storage), Handle(cs, mi, storage)
+    try:
+        for nbands in (None, 7, 300):
+            for strategy in ("window", "atomic"):
+                for tr in (False, True):
+                    _check(m, x, h.run(x, strategy, tr, nbands=nbands), tr, TOL[storage])
+                    np.testing.assert_array_equal(hi.run(xi, strategy, tr, nbands=nbands), _ref(mi, xi, tr))
+        assert cs.csrc_get_info(h.h)["group"] == 16
+        assert cs.csrc_get_info(hi.h)["group"] == 16
+    finally:
+        h.close()
+        hi.close()
+
+
 # --------------------------------------------------------------------------- symmetric values
 def test_symmetric_values(cs):
     rp, c = fe.q1_hex27_pattern(10, 9, 8)
