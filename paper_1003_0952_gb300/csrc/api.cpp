@@ -32,6 +32,10 @@ struct csrc_matrix_s {
   void* d_al = nullptr;
   void* d_au = nullptr;
   void* d_ad = nullptr;
+  // double-float arithmetic: al and au split into (hi, lo) FP32 pairs once, the scatter
+  // operand of the window kernels (the split they would otherwise repeat per pair)
+  void* d_al_df = nullptr;
+  void* d_au_df = nullptr;
   int32_t* d_status = nullptr;
   // partition (Section 3.1 rule) and the window plan built from it
   std::vector<int32_t> part;
@@ -109,7 +113,7 @@ void free_plan(DevPlan& p) {
   dfree(p.band_row); dfree(p.band_plo); dfree(p.band_ntab); dfree(p.band_wp);
   dfree(p.wpage); dfree(p.wbase); dfree(p.wmask);
   dfree(p.acc_row); dfree(p.acc_ptr); dfree(p.acc_src); dfree(p.spill_buf);
-  dfree(p.band_stage); dfree(p.stage_k); dfree(p.stage_r);
+  dfree(p.band_stage); dfree(p.stage_k); dfree(p.stage_r); dfree(p.jslot);
   p = DevPlan();
 }
 
@@ -434,6 +438,30 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
   CSRC_TRY(upload(&p.stage_k, hp.stage_k, s));
   CSRC_TRY(upload(&p.stage_r, hp.stage_r, s));
   CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * rk * h->xbytes())));
+  if (rk == 1 && B == 1) {
+    // window slot of every stored pair: page q of band b's window holds slots q*64 .. q*64+63.
+    // Pairs whose page is outside the window (plans with overflow, which only the atomic
+    // strategy runs) get slot 0.
+    const size_t hcap = ((size_t)h->h + kPairAlign - 1) / kPairAlign * kPairAlign + kPairAlign;
+    std::vector<int32_t> jslot(hcap, 0);
+    std::vector<int32_t> qmap;
+    for (size_t b = 0; b + 1 < hp.band_row.size(); ++b) {
+      const int32_t plo = hp.band_plo[b], ntab = hp.band_ntab[b];
+      qmap.assign((size_t)std::max(ntab, 0), -1);
+      for (int32_t q = hp.band_wp[b]; q < hp.band_wp[b + 1]; ++q) {
+        const int32_t t = hp.wpage[(size_t)q] - plo;
+        if (t >= 0 && t < ntab) qmap[(size_t)t] = q - hp.band_wp[b];
+      }
+      const int64_t k0 = h->ia[(size_t)hp.band_row[b]], k1 = h->ia[(size_t)hp.band_row[b + 1]];
+      for (int64_t k = k0; k < k1; ++k) {
+        const int32_t j = h->ja[(size_t)k];
+        const int32_t t = (j >> kPageShift) - plo;
+        const int32_t q = (t >= 0 && t < ntab) ? qmap[(size_t)t] : -1;
+        jslot[(size_t)k] = q < 0 ? 0 : (q << kPageShift) | (j & (kPageRows - 1));
+      }
+    }
+    CSRC_TRY(upload(&p.jslot, jslot, s));
+  }
   CSRC_TRY(cudaStreamSynchronize(s));
   p.spill = hp.spill;
   p.group = group;
@@ -575,17 +603,21 @@ bool is_device_ptr(const void* p) {
 // for the transpose (Section 5); x and y point at the pass's first column, ldx is their
 // row stride and rk the columns per pass.
 BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, const void* x, void* y, void* spill,
-                   int ldx, int rk) {
+                   int ldx, int rk, bool atomic) {
   BandArgs a;
+  // the window strategy's single-vector plain-row kernels read window slots, and with
+  // double-float arithmetic pre-split scatter operands
+  const bool local = !atomic && rk == 1 && p.block == 1;
   a.n = h->n;
   a.ia = h->d_ia;
-  a.ja = h->d_ja;
+  a.ja = local ? p.jslot : h->d_ja;
   a.band_stage = p.band_stage;
   a.stage_k = p.stage_k;
   a.stage_r = p.stage_r;
   a.group = p.group;
   a.al = transpose ? h->d_au : h->d_al;  // gathered values
   a.au = transpose ? h->d_al : h->d_au;  // scattered values
+  if (local && h->arith == ARITH_DF32) a.au = transpose ? h->d_al_df : h->d_au_df;
   a.ad = h->d_ad;
   a.x = x;
   a.y = y;
@@ -652,7 +684,7 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     DevPlan* p = &h->plan;  // the atomic strategy runs plain rows
     bool covers = h->plan_covers;
     if (atomic) CSRC_TRY_S(plan_b1_for(h, &p, &covers));
-    const BandArgs a = band_args(h, *p, transpose, dx, dy, p->spill_buf, 1, 1);
+    const BandArgs a = band_args(h, *p, transpose, dx, dy, p->spill_buf, 1, 1, atomic);
     if (atomic) CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
                           [&] { return launch_band(h->arith, h->storage, atomic, a, p->nb, p->smem_bytes, s); }));
@@ -697,7 +729,7 @@ csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, boo
     const bool atomic = !covers;  // single column whose plan overflows: atomic strategy
     if (atomic)
       CSRC_TRY(cudaMemset2DAsync(yc, (size_t)nrhs * h->xbytes(), 0, h->xbytes(), (size_t)h->n, s));
-    const BandArgs a = band_args(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk);
+    const BandArgs a = band_args(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk, atomic);
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
                           [&] { return launch_band(h->arith, h->storage, atomic, a, p->nb, p->smem_bytes, s); }));
     if (!atomic && p->nacc > 0)
@@ -803,7 +835,7 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
     if (st != CSRC_OK) return fail(st);
     e->gens.push_back(h->generation);
     const bool atomic = h->tuned == CSRC_STRAT_ATOMIC || !covers;
-    members[(size_t)b] = band_args(h, *p, transpose != 0, X[b], Y[b], p->spill_buf, 1, 1);
+    members[(size_t)b] = band_args(h, *p, transpose != 0, X[b], Y[b], p->spill_buf, 1, 1, atomic);
     // plans with 16 lanes per row run with 8 in the 512-thread batched kernel (64 groups:
     // a stage holds at most 64 rows either way)
     const int lg = p->group == 1 ? 0 : (p->group == 2 ? 1 : (p->group == 4 ? 2 : 3));
@@ -1074,6 +1106,16 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   if ((st = put_values(m->d_al, al)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_ad, ad)) != CSRC_OK) return fail(st);
+  if (m->arith == ARITH_DF32) {
+    if (cudaMalloc(&m->d_al_df, hcap * 8) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+    if (cudaMalloc(&m->d_au_df, hcap * 8) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+    if ((st = from_cuda(launch_split_df(static_cast<const double*>(m->d_al), m->d_al_df, (int64_t)hcap, stream))) !=
+        CSRC_OK)
+      return fail(st);
+    if ((st = from_cuda(launch_split_df(static_cast<const double*>(m->d_au), m->d_au_df, (int64_t)hcap, stream))) !=
+        CSRC_OK)
+      return fail(st);
+  }
   if ((st = from_cuda(cudaStreamSynchronize(stream))) != CSRC_OK) return fail(st);
   m->ia.swap(ia);
   m->ja.swap(ja);
@@ -1112,7 +1154,7 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   if (!h->have_plan || !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
   if (h->plan.spill > capacity) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
-  const BandArgs a = band_args(h, h->plan, transpose, x, y, spill, 1, 1);
+  const BandArgs a = band_args(h, h->plan, transpose, x, y, spill, 1, 1, false);
   CSRC_TRY(launch_band(h->arith, h->storage, false, a, h->plan.nb, h->plan.smem_bytes, s));
   if (h->plan.nacc > 0)
     CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, 1, 1, h->plan.acc_row, h->plan.acc_ptr,
@@ -1504,6 +1546,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   for (int i = 0; i < 3; ++i) free_plan(h->plan_rk[i]);
   free_plan(h->plan_b1);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
+  dfree(h->d_al_df); dfree(h->d_au_df);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);

@@ -143,13 +143,17 @@ struct DevPlan {
   int32_t smem_bytes = 0;      // dynamic shared memory of a band CTA (ring + window + table)
   std::vector<int64_t> band_pairs;  // host copy: stored pairs of each band (batched scheduling)
   int64_t total_pages = 0;
+  // single-vector plans of plain rows: the window slot of every stored pair, written in
+  // place of its column for the window strategy (h entries, padded like ja)
+  int32_t* jslot = nullptr;
 };
 
 // Arguments of the band kernels (passed by value).
 struct BandArgs {
   int32_t n;
   const int32_t* ia;
-  const int32_t* ja;
+  const int32_t* ja;  // columns; window slots (DevPlan::jslot) for the window strategy's
+                      // single-vector plain-row kernels
   const int32_t* band_stage;
   const int32_t* stage_k;
   const int32_t* stage_r;
@@ -159,7 +163,8 @@ struct BandArgs {
   int32_t rk;     // columns per pass (1, 2, 4 or 8); x and y point at the pass's first column
   int32_t block;  // rows per unit (node blocks), 1 for plain rows
   const void* al;  // gathered values  (au for the transpose)
-  const void* au;  // scattered values (al for the transpose)
+  const void* au;  // scattered values (al for the transpose); pre-split double-float
+                   // pairs for the MODE_DF kernels that read window slots
   const void* ad;
   const void* x;
   void* y;
@@ -194,6 +199,9 @@ cudaError_t launch_band_rk(Arith arith, int storage, const BandArgs& a, int nban
 cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, int ldx, const int32_t* acc_row,
                               const int32_t* acc_ptr, const int32_t* acc_src, const void* spill, void* y,
                               cudaStream_t s);
+// out[k] = the double-float split (df32.cuh) of v[k], k < count: the scatter operand of the
+// MODE_DF window kernels, split once when the handle is created.
+cudaError_t launch_split_df(const double* v, void* out, int64_t count, cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
 cudaError_t prepare_band_kernels_block();

@@ -22,6 +22,19 @@ __global__ void accumulate_kernel(int64_t nacc, int rk, int ldx, const int32_t* 
   y[(size_t)row * ldx + c] = s;
 }
 
+// ---------------------------------------------------------------------------- double-float split
+__global__ void split_df_kernel(const double* __restrict__ v, df32* __restrict__ out, int64_t count) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = df_split<false>(v[k], nullptr);
+}
+
+cudaError_t launch_split_df(const double* v, void* out, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 32);
+  split_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, static_cast<df32*>(out), count);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- launchers
 template <int MODE>
 static cudaError_t set_smem_mode() {
