@@ -11,6 +11,8 @@ format the library's ``csrc_create_from_csr`` and the oracle both accept.
 """
 from .generators import (  # noqa: F401
     FEMatrix,
+    RectMatrix,
+    overlap_subdomain,
     splitmix64,
     hash_uniform,
     pattern_from_edges,

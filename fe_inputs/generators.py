@@ -46,6 +46,24 @@ class FEMatrix:
 
 
 # ----------------------------------------------------------------------------- hashing
+@dataclass
+class RectMatrix:
+    """An n-by-m matrix (m >= n) in CSR form (0-based, sorted columns) whose leading
+    n-by-n block has a symmetric pattern: one subdomain of an overlapping decomposition."""
+
+    n: int
+    m: int
+    row_ptr: np.ndarray  # int64[n+1]
+    col: np.ndarray  # int32[nnz], values in [0, m)
+    val: np.ndarray  # float64[nnz]
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+
 def splitmix64(z) -> np.ndarray:
     """SplitMix64 output function applied to counter ``z`` (Steele, Lea & Flood, 2014).
 
@@ -270,6 +288,21 @@ def random_symmetric_pattern(n: int, density: float, seed: int, empty_rows: bool
         i = np.concatenate([i, ring_i])
         j = np.concatenate([j, ring_i - 1])
     return pattern_from_edges(n, i, j)
+
+
+def overlap_subdomain(g: "FEMatrix", n_sub: int, name: str = "") -> RectMatrix:
+    """Rows 0..n_sub-1 of a global FE matrix as one subdomain of an overlapping
+    decomposition: the subdomain's own unknowns keep their numbers 0..n_sub-1 and every
+    other unknown its rows reach (the overlap) is numbered n_sub, n_sub+1, ... in
+    increasing global order, so columns stay sorted within each row."""
+    n_sub = int(min(max(n_sub, 0), g.n))
+    rp = np.ascontiguousarray(g.row_ptr[:n_sub + 1], dtype=np.int64)
+    col = g.col[:int(rp[-1])].astype(np.int64)
+    val = np.array(g.val[:int(rp[-1])], dtype=np.float64)
+    ext = np.unique(col[col >= n_sub])
+    newcol = np.where(col < n_sub, col, n_sub + np.searchsorted(ext, col))
+    return RectMatrix(n_sub, n_sub + len(ext), rp, newcol.astype(np.int32), val, name=name or f"{g.name}_sub{n_sub}",
+                      meta={"global_n": g.n, "overlap": ext.astype(np.int64)})
 
 
 # ----------------------------------------------------------------------------- values

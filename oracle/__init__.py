@@ -13,6 +13,8 @@ Every function cites the paper passage it implements (arXiv:1003.0952):
 - ``csr_to_csrc``: Section 2 (the CSRC layout).
 - ``csrc_spmv``: Fig. 2(a) and Section 2.2.
 - ``csrc_spmv_t``: Section 5 (swap al and au).
+- ``csr_to_csrcr``, ``csrcr_spmv`` and ``csrcr_spmv_t``: Section 2.1 and Fig. 2(b) (rectangular
+  matrices: CSRC square part plus an auxiliary CSR).
 - ``csr_spmv``: Section 1 (the CSR product).
 - ``partition``: Section 3.1 (non-zero guided bands).
 - ``greedy_color`` and ``check_coloring``: Section 3.2 (conflict graph colouring).
@@ -61,6 +63,12 @@ def _load():
                 f.restype = None
                 f.argtypes = [ctypes.c_int64, I64P, I32P, F64P, F64P, F64P, F64P, ctypes.c_int64, F64P,
                               ctypes.c_int64]
+            lib.oracle_csrcr_spmv.restype = None
+            lib.oracle_csrcr_spmv.argtypes = [ctypes.c_int64, I64P, I32P, F64P, F64P, F64P, I64P, I32P, F64P, F64P,
+                                              F64P]
+            lib.oracle_csrcr_spmv_t.restype = None
+            lib.oracle_csrcr_spmv_t.argtypes = [ctypes.c_int64, ctypes.c_int64, I64P, I32P, F64P, F64P, F64P, I64P,
+                                                I32P, F64P, F64P, F64P]
             lib.oracle_csrc_spmm.restype = None
             lib.oracle_csrc_spmm.argtypes = [ctypes.c_int64, I64P, I32P, F64P, F64P, F64P, ctypes.c_int64, F64P,
                                              F64P, ctypes.c_int]
@@ -179,6 +187,90 @@ def csrc_spmm(c: CSRC, X, transpose=False, al=None, au=None, ad=None) -> np.ndar
     lib.oracle_csrc_spmm(n, _p(ia, I64P), _p(ja, I32P), _p(al, F64P), _p(au, F64P), _p(ad, F64P), r,
                          _p(X, F64P), _p(Y, F64P), int(bool(transpose)))
     return Y[:n]
+
+
+class CSRCR:
+    """Rectangular CSRC (Section 2.1): the square CSRC part and the auxiliary CSR."""
+
+    def __init__(self, n, m, square: CSRC, iar, jar, ar):
+        self.n, self.m, self.square, self.iar, self.jar, self.ar = n, m, square, iar, jar, ar
+
+
+def csr_to_csrcr(n, m, row_ptr, col, val) -> CSRCR:
+    """Section 2.1: an n-by-m CSR matrix (m >= n) as A_S + A_R. Columns below n form the
+    structurally symmetric square part A_S (stored as CSRC); columns n..m-1 go to the
+    auxiliary CSR, which keeps their column numbers."""
+    rp, c, v = _i64(row_ptr), _i32(col), _f64(val)
+    if m < n:
+        raise OracleError("a rectangular CSRC matrix needs m >= n")
+    if len(c) and (c.min() < 0 or c.max() >= m):
+        raise OracleError("column index out of range")
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    sq = c < n
+    sq_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows[sq], minlength=n), out=sq_ptr[1:])
+    ar_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows[~sq], minlength=n), out=ar_ptr[1:])
+    square = csr_to_csrc(n, sq_ptr, c[sq], v[sq])
+    return CSRCR(n, m, square, ar_ptr, _i32(c[~sq]), _f64(v[~sq]))
+
+
+def csrcr_spmv(r: CSRCR, x) -> np.ndarray:
+    """Fig. 2(b): y = A x for the rectangular matrix (x has m entries, y has n)."""
+    lib = _load()
+    c = r.square
+    x = _f64(x)
+    assert len(x) == r.m
+    y = np.full(max(r.n, 1), np.nan)
+    ia, ja = _i64(c.ia), _i32(c.ja)
+    al, au, ad = _f64(c.al), _f64(c.au), _f64(c.ad)
+    iar, jar, ar = _i64(r.iar), _i32(r.jar), _f64(r.ar)
+    lib.oracle_csrcr_spmv(r.n, _p(ia, I64P), _p(ja, I32P), _p(al, F64P), _p(au, F64P), _p(ad, F64P),
+                          _p(iar, I64P), _p(jar, I32P), _p(ar, F64P), _p(x, F64P), _p(y, F64P))
+    return y[:r.n]
+
+
+def csrcr_spmv_t(r: CSRCR, x) -> np.ndarray:
+    """y = A^T x for the rectangular matrix (x has n entries, y has m)."""
+    lib = _load()
+    c = r.square
+    x = _f64(x)
+    assert len(x) == r.n
+    y = np.full(max(r.m, 1), np.nan)
+    ia, ja = _i64(c.ia), _i32(c.ja)
+    al, au, ad = _f64(c.al), _f64(c.au), _f64(c.ad)
+    iar, jar, ar = _i64(r.iar), _i32(r.jar), _f64(r.ar)
+    lib.oracle_csrcr_spmv_t(r.n, r.m, _p(ia, I64P), _p(ja, I32P), _p(al, F64P), _p(au, F64P), _p(ad, F64P),
+                            _p(iar, I64P), _p(jar, I32P), _p(ar, F64P), _p(x, F64P), _p(y, F64P))
+    return y[:r.m]
+
+
+def max_rel_err_rect(n, m, row_ptr, col, val, x, y, yref, transpose=False) -> float:
+    """The error metric of ``max_rel_err`` for an n-by-m matrix: per output entry,
+    |y - yref| / sum |a||x| over its row of A (over its column of A for A^T)."""
+    rp, c, v = _i64(row_ptr), _i32(col), np.abs(_f64(val))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    x = np.abs(_f64(x))
+    if transpose:
+        den = np.zeros(m)
+        np.add.at(den, c, v * x[rows])
+    else:
+        den = np.zeros(n)
+        np.add.at(den, rows, v * x[c])
+    d = np.abs(_f64(y) - _f64(yref))
+    if np.isnan(d).any():
+        return float("nan")
+    e = np.where(den > 0, d / np.where(den > 0, den, 1.0), d)
+    return float(e.max()) if len(e) else 0.0
+
+
+def dense_rect(n, m, row_ptr, col, val) -> np.ndarray:
+    """Brute force: the dense n-by-m matrix built entry by entry."""
+    a = np.zeros((n, m))
+    for i in range(n):
+        for p in range(int(row_ptr[i]), int(row_ptr[i + 1])):
+            a[i, int(col[p])] += float(val[p])
+    return a
 
 
 def csr_spmv(n, row_ptr, col, val, x) -> np.ndarray:

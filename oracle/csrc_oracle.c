@@ -116,6 +116,39 @@ void oracle_csrc_spmv_t(int64_t n, const int64_t* ia, const int32_t* ja, const d
   oracle_csrc_spmv(n, ia, ja, au, al, ad, x, incx, y, incy);
 }
 
+/* Section 2.1 and Fig. 2(b): a rectangular n-by-m matrix (m >= n) is A_S + A_R, with
+ * A_S the n-by-n structurally symmetric part in CSRC and A_R the n-by-(m - n) rest in an
+ * auxiliary CSR (iar, jar, ar; jar holds columns in [n, m)). Row i adds the auxiliary
+ * CSR row to the sum t before it is assigned. x has m entries, y has n. */
+void oracle_csrcr_spmv(int64_t n, const int64_t* ia, const int32_t* ja, const double* al,
+                       const double* au, const double* ad, const int64_t* iar, const int32_t* jar,
+                       const double* ar, const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double xi = x[i];
+    double t = ad[i] * xi;
+    for (int64_t k = ia[i]; k < ia[i + 1]; ++k) {
+      int64_t j = ja[k];
+      t = t + al[k] * x[j];
+      y[j] = y[j] + au[k] * xi;
+    }
+    for (int64_t k = iar[i]; k < iar[i + 1]; ++k) t = t + ar[k] * x[jar[k]];
+    y[i] = t;
+  }
+}
+
+/* The transpose of the rectangular matrix, y = A^T x with x of n entries and y of m:
+ * entries 0..n-1 are A_S^T x (Section 5: al and au swapped), entries n..m-1 are
+ * A_R^T x, i.e. column c of A_R scattered by rows: y[c] += ar(k) x(i) for every
+ * auxiliary entry (i, c), y[n..m-1] starting from zero. */
+void oracle_csrcr_spmv_t(int64_t n, int64_t m, const int64_t* ia, const int32_t* ja, const double* al,
+                         const double* au, const double* ad, const int64_t* iar, const int32_t* jar,
+                         const double* ar, const double* x, double* y) {
+  oracle_csrc_spmv(n, ia, ja, au, al, ad, x, 1, y, 1);
+  for (int64_t c = n; c < m; ++c) y[c] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = iar[i]; k < iar[i + 1]; ++k) y[jar[k]] = y[jar[k]] + ar[k] * x[i];
+}
+
 /* Several right-hand sides: Y = A X (or A^T X), X and Y n-by-r row-major, one
  * Fig. 2(a) product per column. */
 void oracle_csrc_spmm(int64_t n, const int64_t* ia, const int32_t* ja, const double* al,

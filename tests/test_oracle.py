@@ -189,6 +189,103 @@ def test_p1_triangle_stiffness_closed_forms():
 
 
 # --------------------------------------------------------------------------- several right-hand sides
+# --------------------------------------------------------------------------- Section 2.1 / Fig. 2(b)
+def _random_rect(n, extra, density, seed, integer=False):
+    """Square symmetric pattern plus random entries in `extra` extra columns."""
+    rp, c = fe.random_symmetric_pattern(n, density, seed)
+    rng = np.random.default_rng(seed + 100)
+    rows = [list(c[rp[i]:rp[i + 1]]) for i in range(n)]
+    for i in range(n):
+        if extra:
+            k = int(rng.integers(0, min(extra, 4) + 1))
+            rows[i] += sorted(set(int(v) for v in n + rng.integers(0, extra, size=k)))
+    ptr = np.zeros(n + 1, np.int64)
+    ptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([v for r in rows for v in r], dtype=np.int32)
+    if integer:
+        val = rng.integers(-8, 9, size=len(col)).astype(np.float64)
+    else:
+        val = rng.uniform(-1.0, 1.0, size=len(col))
+    return fe.RectMatrix(n, n + extra, ptr, col, val)
+
+
+RECT = [(1, 0, 0.0, 1), (1, 3, 0.0, 2), (5, 2, 0.5, 3), (9, 7, 0.4, 4), (33, 5, 0.2, 5), (64, 40, 0.1, 6)]
+
+
+@pytest.mark.parametrize("n,extra,density,seed", RECT)
+def test_rectangular_product_matches_dense_brute_force(n, extra, density, seed):
+    a = _random_rect(n, extra, density, seed)
+    r = oracle.csr_to_csrcr(a.n, a.m, a.row_ptr, a.col, a.val)
+    d = oracle.dense_rect(a.n, a.m, a.row_ptr, a.col, a.val)
+    x = fe.source_vector(a.m, seed)
+    np.testing.assert_allclose(oracle.csrcr_spmv(r, x), d @ x, rtol=1e-13, atol=1e-13)
+    xt = fe.source_vector(a.n, seed + 1)
+    np.testing.assert_allclose(oracle.csrcr_spmv_t(r, xt), d.T @ xt, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,extra,density,seed", RECT)
+def test_rectangular_integer_values_exact_and_bilinear(n, extra, density, seed):
+    a = _random_rect(n, extra, density, seed, integer=True)
+    r = oracle.csr_to_csrcr(a.n, a.m, a.row_ptr, a.col, a.val)
+    d = oracle.dense_rect(a.n, a.m, a.row_ptr, a.col, a.val)
+    x = fe.integer_vector(a.m, seed)
+    u = fe.integer_vector(a.n, seed + 2)
+    y = oracle.csrcr_spmv(r, x)
+    np.testing.assert_array_equal(y, d @ x)
+    # the CSR product of the whole n-by-m matrix (Section 1) gives the same rows
+    np.testing.assert_array_equal(y, oracle.csr_spmv(a.n, a.row_ptr, a.col, a.val, x))
+    yt = oracle.csrcr_spmv_t(r, u)
+    np.testing.assert_array_equal(yt, d.T @ u)
+    assert float(u @ y) == float(yt @ x)  # u^T (A x) = (A^T u)^T x, exact in integers
+
+
+def test_rectangular_without_extra_columns_is_the_square_product():
+    m = _random_matrix(33, 0.3, 11)
+    r = oracle.csr_to_csrcr(m.n, m.n, m.row_ptr, m.col, m.val)
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, 12)
+    np.testing.assert_array_equal(oracle.csrcr_spmv(r, x), oracle.csrc_spmv(c, x))
+    np.testing.assert_array_equal(oracle.csrcr_spmv_t(r, x), oracle.csrc_spmv_t(c, x))
+
+
+def test_overlap_subdomain_rows_equal_the_global_product():
+    # one subdomain of an overlapping decomposition: its rows of the global product, with x
+    # zero outside the subdomain and its overlap
+    g = fe.q1_hex(6, 3, 13)
+    a = fe.overlap_subdomain(g, g.n // 2)
+    assert a.m > a.n
+    r = oracle.csr_to_csrcr(a.n, a.m, a.row_ptr, a.col, a.val)
+    xs = fe.integer_vector(a.m, 14)
+    xg = np.zeros(g.n)
+    xg[:a.n] = xs[:a.n]
+    xg[a.meta["overlap"]] = xs[a.n:]
+    yg = oracle.csrc_spmv(oracle.from_matrix(fe.FEMatrix(g.n, g.row_ptr, g.col,
+                                                         np.round(g.val * 8.0))), xg)
+    ar = fe.RectMatrix(a.n, a.m, a.row_ptr, a.col, np.round(a.val * 8.0))
+    rr = oracle.csr_to_csrcr(ar.n, ar.m, ar.row_ptr, ar.col, ar.val)
+    np.testing.assert_array_equal(oracle.csrcr_spmv(rr, xs), yg[:a.n])
+    # the square part is the global matrix's leading principal block
+    sq = sp.csr_matrix((g.val, g.col, g.row_ptr), shape=(g.n, g.n))[:a.n, :a.n].tocsr()
+    sq.sort_indices()
+    np.testing.assert_array_equal(r.square.ad, sq.diagonal())
+
+
+def test_rectangular_error_metric_and_rejections():
+    a = _random_rect(9, 7, 0.4, 21)
+    r = oracle.csr_to_csrcr(a.n, a.m, a.row_ptr, a.col, a.val)
+    x = fe.source_vector(a.m, 22)
+    y = oracle.csrcr_spmv(r, x)
+    assert oracle.max_rel_err_rect(a.n, a.m, a.row_ptr, a.col, a.val, x, y, y) == 0.0
+    # dropping one auxiliary term is seen at the level of that term
+    i = int(np.argmax(np.diff(r.iar)))
+    k = int(r.iar[i])
+    bad = y.copy()
+    bad[i] -= r.ar[k] * x[r.jar[k]]
+    assert oracle.max_rel_err_rect(a.n, a.m, a.row_ptr, a.col, a.val, x, bad, y) > 1e-3
+    with pytest.raises(oracle.OracleError):
+        oracle.csr_to_csrcr(a.n, a.n - 1, a.row_ptr, a.col, a.val)
+
+
 def test_spmm_columns_match_dense():
     m = _random_matrix(30, 0.2, 21)
     c = oracle.from_matrix(m)
