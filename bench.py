@@ -444,7 +444,7 @@ def run_suite(args):
             finally:
                 cs.csrc_destroy(h)
 
-    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5"}
+    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1"}
     if "c1" in sel:
         m, _ = build_workload("p1_100x100")
         spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
@@ -483,6 +483,34 @@ def run_suite(args):
             finally:
                 cs.csrc_destroy(h)
         del m
+    if "n1" in sel:
+        # rectangular CSRC (Section 2.1): the first half of q1v_96's rows as one subdomain of an
+        # overlapping decomposition, its overlap columns in the auxiliary CSR
+        g, _ = build_workload("q1v_96")
+        a = fe.overlap_subdomain(g, g.n // 2, "q1v_96_half")
+        del g
+        h = cs.csrc_create_rect_from_csr(a.n, a.m, a.row_ptr, a.col, a.val, cs.CSRC_F64)
+        try:
+            cs.csrc_partition(h, 0)
+            xm = torch.from_numpy(fe.source_vector(a.m, 10)).cuda()
+            xn = torch.from_numpy(fe.source_vector(a.n, 11)).cuda()
+            yn = torch.empty(a.n, dtype=torch.float64, device="cuda")
+            ym = torch.empty(a.m, dtype=torch.float64, device="cuda")
+            info = cs.csrc_get_info(h)
+            mb = info["model_bytes"]
+            for tr in (False, True):
+                if tr:
+                    ms = _events_ms(lambda: cs.csrc_spmv_t(h, xn, ym, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+                else:
+                    ms = _events_ms(lambda: cs.csrc_spmv(h, xm, yn, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+                emit({"suite": "N1 rectangular CSRC: q1v_96 half-domain with overlap", "n": a.n, "m": a.m,
+                      "aux_nnz": info["rect_nnz"], "storage": "f64", "strategy": "window",
+                      "product": "A^T x" if tr else "A x", "ms_per_product": ms, "GB/s": mb / ms / 1e6})
+            if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
+                raise RuntimeError("device status")
+        finally:
+            cs.csrc_destroy(h)
+        del a
     if "c5" in sel:
         ms_list = fe.batch_meshes(256, 1005)
         tot_n = sum(m.n for m in ms_list)
@@ -533,7 +561,8 @@ def main(argv=None):
                     help="value storage: f64 (the default workload), or f32 / bf16 with float vectors")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--suite", default=None, help="all, or a comma list of c1..c5: one JSON line per configuration row")
+    ap.add_argument("--suite", default=None,
+                    help="all, or a comma list of c1..c5, n1: one JSON line per configuration row")
     ap.add_argument("--suite-iters", type=int, default=20)
     ap.add_argument("--tet-method", default="delaunay", choices=["delaunay", "kuhn"])
     args = ap.parse_args(argv)

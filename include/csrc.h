@@ -103,6 +103,8 @@ typedef struct {
   int32_t group;            /* lanes per row of the band kernel (0 before the plan is built) */
   int64_t nstages;          /* shared-memory ring stages of one single-vector product */
   int32_t block;            /* rows per node block the single-vector product runs (1 = plain rows) */
+  int64_t m;                /* columns: n for square handles, m >= n for rectangular ones */
+  int64_t rect_nnz;         /* entries of the auxiliary CSR of a rectangular handle (0 when square) */
 } csrc_info;
 
 /*
@@ -122,6 +124,28 @@ typedef struct {
  */
 csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row_ptr, const int32_t* col,
                                  const double* val, csrc_dtype storage, uint32_t flags, cudaStream_t stream);
+
+/*
+ * Build a handle for a rectangular n-by-m matrix, m >= n (Section 2.1, Fig. 2(b)): the
+ * n-by-n block of columns 0..n-1 (A_S) must have a symmetric pattern and is stored as
+ * CSRC exactly as csrc_create_from_csr stores a square matrix; the entries of columns
+ * n..m-1 (A_R) go to an auxiliary CSR, plus a column-major copy of it for A^T. This is
+ * the matrix of one subdomain in an overlapping decomposition: its own unknowns first,
+ * then the overlap.
+ *   n, m     rows and columns, 0 <= n <= m < 2^31
+ *   row_ptr  host, int64[n+1]; col host, int32[row_ptr[n]] in [0, m), strictly ascending
+ *            within each row; val host, double[row_ptr[n]]; base as csrc_create_from_csr
+ * On the handle, csrc_spmv reads x of m entries and writes y of n (A_S x[0..n) by the
+ * chosen strategy, then each row adds its A_R row), and csrc_spmv_t reads x of n entries
+ * and writes y of m (A_S^T x into y[0..n), A_R^T x into y[n..m)). Partition, colouring,
+ * autotuning and profiling work as for a square handle (they concern A_S).
+ * csrc_spmm_batched, csrc_autotune_spmm and csrc_spmv_noalloc return INVALID_ARG for
+ * rectangular handles.
+ * Errors: as csrc_create_from_csr, and INVALID_ARG when m < n. On error *out is NULL.
+ */
+csrc_status csrc_create_rect_from_csr(csrc_handle* out, int32_t n, int32_t m, const int64_t* row_ptr,
+                                      const int32_t* col, const double* val, csrc_dtype storage, uint32_t flags,
+                                      cudaStream_t stream);
 
 /*
  * Build a handle from coordinate triples (host arrays of nnz entries, any order).

@@ -60,7 +60,7 @@ class csrc_info(ctypes.Structure):
         ("spill_rows", ctypes.c_int64), ("accum_bytes", ctypes.c_int64), ("max_window_slots", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("tuned_strategy", ctypes.c_int32),
         ("tuned_rk", ctypes.c_int32), ("group", ctypes.c_int32), ("nstages", ctypes.c_int64),
-        ("block", ctypes.c_int32),
+        ("block", ctypes.c_int32), ("m", ctypes.c_int64), ("rect_nnz", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -83,6 +83,8 @@ SIGNATURES = {
     "csrc_create_from_csr": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int, ctypes.c_uint32, _VP]),
     "csrc_create_from_coo": (ctypes.c_int, [_P(_VP), ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, ctypes.c_int,
                                             ctypes.c_uint32, _VP]),
+    "csrc_create_rect_from_csr": (ctypes.c_int, [_P(_VP), ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int,
+                                                 ctypes.c_uint32, _VP]),
     "csrc_partition": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
     "csrc_color": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(ctypes.c_int32), _VP]),
     "csrc_spmv": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -165,6 +167,19 @@ def csrc_create_from_csr(n, row_ptr, col, val, storage=CSRC_F64, flags=0, stream
     h = _VP()
     _check(_lib.csrc_create_from_csr(ctypes.byref(h), int(n), _ptr(row_ptr), _ptr(col), _ptr(val), int(storage),
                                      int(flags), _stream(stream)), "csrc_create_from_csr")
+    return h.value
+
+
+def csrc_create_rect_from_csr(n, m, row_ptr, col, val, storage=CSRC_F64, flags=0, stream=None) -> int:
+    """Rectangular n-by-m matrix (m >= n): row_ptr int64[n+1], col int32[nnz] in [0, m),
+    val float64[nnz], host numpy arrays. Products read x of m entries (A x) or n (A^T x)."""
+    import numpy as np
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    h = _VP()
+    _check(_lib.csrc_create_rect_from_csr(ctypes.byref(h), int(n), int(m), _ptr(row_ptr), _ptr(col), _ptr(val),
+                                          int(storage), int(flags), _stream(stream)), "csrc_create_rect_from_csr")
     return h.value
 
 

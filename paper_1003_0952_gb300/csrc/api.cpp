@@ -37,6 +37,19 @@ struct csrc_matrix_s {
   void* d_al_df = nullptr;
   void* d_au_df = nullptr;
   int32_t* d_status = nullptr;
+  // rectangular matrices (Section 2.1): m columns, the auxiliary CSR of columns n..m-1 for
+  // the rows that have any (d_rrow, d_rptr, d_rcol, d_rval) and its column-major copy
+  int32_t m = 0;
+  int64_t rnnz = 0;
+  int32_t nrrows = 0;
+  int32_t* d_rrow = nullptr;
+  int32_t* d_rptr = nullptr;
+  int32_t* d_rcol = nullptr;
+  void* d_rval = nullptr;
+  int32_t* d_tptr = nullptr;
+  int32_t* d_trow = nullptr;
+  void* d_tval = nullptr;
+  bool rect() const { return m != n; }
   // partition (Section 3.1 rule) and the window plan built from it
   std::vector<int32_t> part;
   DevPlan plan;
@@ -641,36 +654,46 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
 csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st, cudaStream_t s, bool transpose) {
   if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
   if (st < CSRC_STRAT_AUTO || st > CSRC_STRAT_ATOMIC) return CSRC_ERR_INVALID_ARG;
-  if (h->n == 0) return CSRC_OK;
+  if (h->m == 0) return CSRC_OK;
+  // x and y lengths: n each, or m and n (A x) / n and m (A^T x) for a rectangular matrix
   const size_t vb = (size_t)h->n * h->xbytes();
+  const size_t xb = (size_t)(transpose ? h->n : h->m) * h->xbytes();
+  const size_t yb = (size_t)(transpose ? h->m : h->n) * h->xbytes();
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
-  if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
+  if (xa < ya + yb && ya < xa + xb) return CSRC_ERR_ALIAS;
   CSRC_TRY_S(ensure_device(h));
-  if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
+  if (h->n == 0) {  // no square part: only A_R^T x can be non-zero
+    if (!transpose) return CSRC_OK;
+  } else if (!h->have_plan) {
+    CSRC_TRY_S(make_plan(h, 0));
+  }
   csrc_strategy strat = st;
   if (strat == CSRC_STRAT_AUTO) strat = h->tuned ? (csrc_strategy)h->tuned : CSRC_STRAT_WINDOW;
-  if (strat == CSRC_STRAT_WINDOW && !h->plan_covers) {
+  if (h->n > 0 && strat == CSRC_STRAT_WINDOW && !h->plan_covers) {
     if (st == CSRC_STRAT_AUTO) strat = CSRC_STRAT_ATOMIC;
     else return CSRC_ERR_NOT_PARTITIONED;
   }
-  if (strat == CSRC_STRAT_COLOR && h->ncolors == 0) return CSRC_ERR_NOT_COLORED;
-  // host vectors are staged through handle-owned device buffers
+  if (h->n > 0 && strat == CSRC_STRAT_COLOR && h->ncolors == 0) return CSRC_ERR_NOT_COLORED;
+  // host vectors are staged through handle-owned device buffers (m entries: room for either)
+  const size_t sb = (size_t)h->m * h->xbytes();
   const bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
   const void* dx = x;
   void* dy = y;
   if (!xdev) {
-    if (!h->d_xs) CSRC_TRY(cudaMalloc(&h->d_xs, vb));
-    CSRC_TRY(cudaMemcpyAsync(h->d_xs, x, vb, cudaMemcpyHostToDevice, s));
+    if (!h->d_xs) CSRC_TRY(cudaMalloc(&h->d_xs, sb));
+    CSRC_TRY(cudaMemcpyAsync(h->d_xs, x, xb, cudaMemcpyHostToDevice, s));
     dx = h->d_xs;
   }
   if (!ydev) {
-    if (!h->d_ys) CSRC_TRY(cudaMalloc(&h->d_ys, vb));
+    if (!h->d_ys) CSRC_TRY(cudaMalloc(&h->d_ys, sb));
     dy = h->d_ys;
   }
   const void* g = transpose ? h->d_au : h->d_al;  // gathered values
   const void* sc = transpose ? h->d_al : h->d_au; // scattered values
-  if (strat == CSRC_STRAT_COLOR) {
+  if (h->n == 0) {
+    // nothing to do for A_S
+  } else if (strat == CSRC_STRAT_COLOR) {
     CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     for (int32_t c = 0; c < h->ncolors; ++c) {
       const int32_t a = h->color_ptr[c], b = h->color_ptr[c + 1];
@@ -694,7 +717,20 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
                                  p->spill_buf, dy, s);
       }));
   }
-  if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, vb, cudaMemcpyDeviceToHost, s));
+  // the auxiliary CSR of a rectangular matrix: A_R x added to y[0..n), or A_R^T x into y[n..m)
+  if (h->rect()) {
+    if (!transpose) {
+      CSRC_TRY(timed_launch(h, CSRC_KERNEL_OTHER, s, [&] {
+        return launch_rect_rows(h->storage, h->nrrows, h->d_rrow, h->d_rptr, h->d_rcol, h->d_rval, dx, dy, s);
+      }));
+    } else {
+      CSRC_TRY(timed_launch(h, CSRC_KERNEL_OTHER, s, [&] {
+        return launch_rect_cols(h->storage, h->m - h->n, h->n, h->d_tptr, h->d_trow, h->d_tval, dx, dy, s);
+      }));
+    }
+  }
+  (void)vb;
+  if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, yb, cudaMemcpyDeviceToHost, s));
   return CSRC_OK;
 }
 
@@ -1036,6 +1072,7 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   csrc_matrix_s* m = new (std::nothrow) csrc_matrix_s();
   if (!m) return CSRC_ERR_OUT_OF_MEMORY;
   m->n = n;
+  m->m = n;
   m->h = h64;
   m->storage = storage;
   m->flags = flags;
@@ -1145,7 +1182,7 @@ int32_t handle_device(const csrc_matrix_s* h) { return h->device; }
 // and x, y must be device pointers. The device of the handle must be current.
 csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool transpose, void* spill,
                                 int64_t capacity, cudaStream_t s) {
-  if (!h || !x || !y || !spill) return CSRC_ERR_INVALID_ARG;
+  if (!h || !x || !y || !spill || h->rect()) return CSRC_ERR_INVALID_ARG;
   if (h->n == 0) return CSRC_OK;
   const size_t vb = (size_t)h->n * h->xbytes();
   const char* xa = static_cast<const char*>(x);
@@ -1190,6 +1227,113 @@ csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row
   }
   try {
     return create_from_host_csr(out, n, row_ptr, col, val, storage, flags, stream);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_create_rect_from_csr(csrc_handle* out, int32_t n, int32_t m, const int64_t* row_ptr,
+                                      const int32_t* col, const double* val, csrc_dtype storage, uint32_t flags,
+                                      cudaStream_t stream) {
+  if (!out) return CSRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || m < n || !row_ptr) return CSRC_ERR_INVALID_ARG;
+  if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
+                         CSRC_FLAG_NODE_BLOCKS))
+    return CSRC_ERR_INVALID_ARG;
+  const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
+  if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return CSRC_ERR_INVALID_ARG;
+  const int64_t nnz = row_ptr[n] - base;
+  if (nnz > 0 && (!col || !val)) return CSRC_ERR_INVALID_ARG;
+  try {
+    // Section 2.1: columns below n form A_S, the others A_R (0-based from here on)
+    std::vector<int64_t> sptr((size_t)n + 1, 0);
+    std::vector<int32_t> scol, rrow, rptr{0}, rcol;
+    std::vector<double> sval, rval;
+    for (int32_t i = 0; i < n; ++i) {
+      bool any = false;
+      for (int64_t p = row_ptr[i] - base; p < row_ptr[i + 1] - base; ++p) {
+        const int64_t c = (int64_t)col[p] - base;
+        if (c < 0 || c >= m) return CSRC_ERR_INDEX_RANGE;
+        if (p > row_ptr[i] - base && c <= (int64_t)col[p - 1] - base) return CSRC_ERR_DUPLICATE;
+        if (c < n) {
+          scol.push_back((int32_t)c);
+          sval.push_back(val[p]);
+        } else {
+          rcol.push_back((int32_t)c);
+          rval.push_back(val[p]);
+          any = true;
+        }
+      }
+      sptr[(size_t)i + 1] = (int64_t)scol.size();
+      if (any) {
+        if (rcol.size() > (size_t)INT32_MAX - 1) return CSRC_ERR_INVALID_ARG;
+        rrow.push_back(i);
+        rptr.push_back((int32_t)rcol.size());
+      }
+    }
+    csrc_handle h = nullptr;
+    CSRC_TRY_S(create_from_host_csr(&h, n, sptr.data(), scol.data(), sval.data(), storage,
+                                    flags & ~(uint32_t)CSRC_FLAG_ONE_BASED, stream));
+    h->m = m;
+    h->rnnz = (int64_t)rcol.size();
+    h->nrrows = (int32_t)rrow.size();
+    // column-major copy of A_R for A^T x: columns n..m-1, rows ascending within a column
+    std::vector<int32_t> tptr((size_t)(m - n) + 1, 0), trow(rcol.size());
+    std::vector<double> tval(rcol.size());
+    for (int32_t c : rcol) tptr[(size_t)(c - n) + 1]++;
+    for (size_t c = 0; c + 1 < tptr.size(); ++c) tptr[c + 1] += tptr[c];
+    {
+      std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
+      for (size_t t = 0; t < rrow.size(); ++t)
+        for (int32_t k = rptr[t]; k < rptr[t + 1]; ++k) {
+          const int32_t q = fill[(size_t)(rcol[(size_t)k] - n)]++;
+          trow[(size_t)q] = rrow[t];
+          tval[(size_t)q] = rval[(size_t)k];
+        }
+    }
+    auto values = [&](void** dst, const std::vector<double>& v) -> cudaError_t {
+      const size_t cnt = std::max<size_t>(1, v.size());
+      if (storage == CSRC_F64) {
+        cudaError_t e = cudaMalloc(dst, cnt * 8);
+        if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice);
+        return e;
+      }
+      if (storage == CSRC_F32) {
+        std::vector<float> t(v.size());
+        for (size_t i = 0; i < v.size(); ++i) t[i] = (float)v[i];
+        cudaError_t e = cudaMalloc(dst, cnt * 4);
+        if (e == cudaSuccess && !t.empty()) e = cudaMemcpy(*dst, t.data(), t.size() * 4, cudaMemcpyHostToDevice);
+        return e;
+      }
+      std::vector<uint16_t> t(v.size());
+      for (size_t i = 0; i < v.size(); ++i) t[i] = f64_to_bf16(v[i]);
+      cudaError_t e = cudaMalloc(dst, cnt * 2);
+      if (e == cudaSuccess && !t.empty()) e = cudaMemcpy(*dst, t.data(), t.size() * 2, cudaMemcpyHostToDevice);
+      return e;
+    };
+    cudaError_t e = cudaSuccess;
+    auto ints = [&](int32_t** dst, const std::vector<int32_t>& v) {
+      if (e != cudaSuccess) return;
+      e = dmalloc(dst, v.size());
+      if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * 4, cudaMemcpyHostToDevice);
+    };
+    ints(&h->d_rrow, rrow);
+    ints(&h->d_rptr, rptr);
+    ints(&h->d_rcol, rcol);
+    ints(&h->d_tptr, tptr);
+    ints(&h->d_trow, trow);
+    if (e == cudaSuccess) e = values(&h->d_rval, rval);
+    if (e == cudaSuccess) e = values(&h->d_tval, tval);
+    if (e != cudaSuccess) {
+      csrc_destroy(h);
+      return from_cuda(e);
+    }
+    *out = h;
+    return CSRC_OK;
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
   }
@@ -1348,6 +1492,7 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
   if (batch < 0 || nrhs <= 0 || (batch > 0 && (!hs || !X || !Y))) return CSRC_ERR_INVALID_ARG;
   for (int32_t b = 0; b < batch; ++b) {
     if (!hs[b] || !X[b] || !Y[b]) return CSRC_ERR_INVALID_ARG;
+    if (hs[b]->rect()) return CSRC_ERR_INVALID_ARG;  // rectangular matrices run single products
     if (hs[b]->storage != hs[0]->storage) return CSRC_ERR_MISMATCH;
   }
   if (batch == 0) return CSRC_OK;
@@ -1419,7 +1564,7 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
 }
 
 csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream) {
-  if (!h || !X || !Y || nrhs <= 0) return CSRC_ERR_INVALID_ARG;
+  if (!h || !X || !Y || nrhs <= 0 || h->rect()) return CSRC_ERR_INVALID_ARG;
   CSRC_TRY_S(ensure_device(h));
   if (h->n == 0 || nrhs == 1) return CSRC_OK;
   try {
@@ -1521,6 +1666,10 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   info->group = h->have_plan ? h->plan.group : 0;
   info->block = h->have_plan ? h->plan.block : h->block;
   info->nstages = h->have_plan ? h->plan.nstages : 0;
+  info->m = h->m;
+  info->rect_nnz = h->rnnz;
+  if (h->rect())  // the auxiliary CSR: compact row list and pointers, columns, values, x of the overlap
+    info->model_bytes += 8 * (int64_t)h->nrrows + 4 + (4 + vb) * h->rnnz + xb * ((int64_t)h->m - h->n);
   return CSRC_OK;
 }
 
@@ -1547,6 +1696,8 @@ csrc_status csrc_destroy(csrc_handle h) {
   free_plan(h->plan_b1);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_al_df); dfree(h->d_au_df);
+  dfree(h->d_rrow); dfree(h->d_rptr); dfree(h->d_rcol); dfree(h->d_rval);
+  dfree(h->d_tptr); dfree(h->d_trow); dfree(h->d_tval);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);

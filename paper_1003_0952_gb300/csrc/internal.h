@@ -202,6 +202,12 @@ cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, in
 // out[k] = the double-float split (df32.cuh) of v[k], k < count: the scatter operand of the
 // MODE_DF window kernels, split once when the handle is created.
 cudaError_t launch_split_df(const double* v, void* out, int64_t count, cudaStream_t s);
+// The auxiliary CSR of a rectangular matrix (rect.cu): y[rows[t]] += row t of A_R times x,
+// and y[n + c] = column c of A_R times x (column-major copy), FP64 for FP64 storage.
+cudaError_t launch_rect_rows(int storage, int32_t nrows, const int32_t* rows, const int32_t* ptr, const int32_t* col,
+                             const void* val, const void* x, void* y, cudaStream_t s);
+cudaError_t launch_rect_cols(int storage, int32_t ncols, int32_t n, const int32_t* ptr, const int32_t* row,
+                             const void* val, const void* x, void* y, cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
 cudaError_t prepare_band_kernels_block();

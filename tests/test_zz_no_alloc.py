@@ -127,3 +127,18 @@ def test_rejections(cs):
         assert e.value.status == cs.CSRC_ERR_INVALID_ARG
     finally:
         cs.csrc_destroy(h)
+
+
+def test_rectangular_handle_is_rejected(cs):
+    g = fe.q1_hex(6, 1, 41)
+    a = fe.overlap_subdomain(g, g.n // 2)
+    h = cs.csrc_create_rect_from_csr(a.n, a.m, a.row_ptr, a.col, a.val, cs.CSRC_F64)
+    try:
+        cs.csrc_partition(h, 0)
+        x = torch.zeros(a.m, dtype=torch.float64, device="cuda")
+        y = torch.zeros(a.m, dtype=torch.float64, device="cuda")
+        with pytest.raises(cs.CsrcError) as e:
+            cs.csrc_spmv_noalloc(h, x, y, False, torch.cuda.current_stream())
+        assert e.value.status == cs.CSRC_ERR_INVALID_ARG
+    finally:
+        cs.csrc_destroy(h)
