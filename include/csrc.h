@@ -61,7 +61,8 @@ typedef enum {
   CSRC_ERR_DEVICE_TIMEOUT = 10,      /* a bounded device wait ran out (device status word) */
   CSRC_ERR_DEVICE_BOUNDS = 11,       /* a device-side index check failed (device status word) */
   CSRC_ERR_RANGE = 12,               /* an x value lies outside the double-float range (device status word) */
-  CSRC_ERR_MISMATCH = 13             /* batch members differ in storage type */
+  CSRC_ERR_MISMATCH = 13,            /* batch members differ in storage type */
+  CSRC_ERR_NOT_NUM_SYMMETRIC = 14    /* CSRC_FLAG_SYMMETRIC_VALUES set but some a_ij != a_ji */
 } csrc_status;
 
 typedef enum { CSRC_F64 = 0, CSRC_F32 = 1, CSRC_BF16 = 2 } csrc_dtype; /* storage of ad, al, au */
@@ -78,6 +79,10 @@ enum {
   CSRC_FLAG_ONE_BASED = 2,   /* row_ptr / row / col are 1-based (Fortran, as in Fig. 2) */
   CSRC_FLAG_FP64_ARITH = 4,  /* CSRC_F64 only: multiply and add on the FP64 pipe (bit-for-bit IEEE
                                 double products) instead of the default double-float arithmetic */
+  CSRC_FLAG_SYMMETRIC_VALUES = 16, /* numerically symmetric matrix (Section 2.2): every a_ji equals a_ij
+                                     bit for bit (checked at creation), au is not stored and the
+                                     kernels scatter with al, so a product streams 12 instead of 20
+                                     bytes per pair in FP64; A^T x = A x */
   CSRC_FLAG_NODE_BLOCKS = 8  /* when the matrix has node blocks (B = 2 or 3 consecutive rows sharing
                                 their columns, as with B unknowns per FE node), run node-block units */
 };

@@ -33,6 +33,7 @@ CSRC_ERR_DEVICE_TIMEOUT = 10
 CSRC_ERR_DEVICE_BOUNDS = 11
 CSRC_ERR_RANGE = 12
 CSRC_ERR_MISMATCH = 13
+CSRC_ERR_NOT_NUM_SYMMETRIC = 14
 
 # storage (csrc_dtype)
 CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
@@ -40,6 +41,7 @@ CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
 CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC = 0, 1, 2, 3
 # flags
 CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH, CSRC_FLAG_NODE_BLOCKS = 1, 2, 4, 8
+CSRC_FLAG_SYMMETRIC_VALUES = 16
 
 STRATEGIES = {"auto": CSRC_STRAT_AUTO, "window": CSRC_STRAT_WINDOW, "color": CSRC_STRAT_COLOR,
               "atomic": CSRC_STRAT_ATOMIC}

@@ -30,8 +30,10 @@ struct csrc_matrix_s {
   int32_t* d_ia = nullptr;
   int32_t* d_ja = nullptr;
   void* d_al = nullptr;
-  void* d_au = nullptr;
+  void* d_au = nullptr;        // null for numerically symmetric storage (al serves both)
   void* d_ad = nullptr;
+  bool sym = false;            // CSRC_FLAG_SYMMETRIC_VALUES: au is al (Section 2.2)
+  void* au_ptr() const { return sym ? d_al : d_au; }
   // double-float arithmetic: al and au split into (hi, lo) FP32 pairs once, the scatter
   // operand of the window kernels (the split they would otherwise repeat per pair)
   void* d_al_df = nullptr;
@@ -628,9 +630,9 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
   a.stage_k = p.stage_k;
   a.stage_r = p.stage_r;
   a.group = p.group;
-  a.al = transpose ? h->d_au : h->d_al;  // gathered values
-  a.au = transpose ? h->d_al : h->d_au;  // scattered values
-  if (local && h->arith == ARITH_DF32) a.au = transpose ? h->d_al_df : h->d_au_df;
+  a.al = transpose ? h->au_ptr() : h->d_al;  // gathered values
+  a.au = transpose ? h->d_al : h->au_ptr();  // scattered values (the same array when symmetric)
+  if (local && h->arith == ARITH_DF32 && !h->sym) a.au = transpose ? h->d_al_df : h->d_au_df;
   a.ad = h->d_ad;
   a.x = x;
   a.y = y;
@@ -689,8 +691,8 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     if (!h->d_ys) CSRC_TRY(cudaMalloc(&h->d_ys, sb));
     dy = h->d_ys;
   }
-  const void* g = transpose ? h->d_au : h->d_al;  // gathered values
-  const void* sc = transpose ? h->d_al : h->d_au; // scattered values
+  const void* g = transpose ? h->au_ptr() : h->d_al;  // gathered values
+  const void* sc = transpose ? h->d_al : h->au_ptr(); // scattered values
   if (h->n == 0) {
     // nothing to do for A_S
   } else if (strat == CSRC_STRAT_COLOR) {
@@ -1077,6 +1079,14 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   m->storage = storage;
   m->flags = flags;
   m->block = (flags & CSRC_FLAG_NODE_BLOCKS) ? detect_node_blocks(n, ia, ja) : 1;
+  if (flags & CSRC_FLAG_SYMMETRIC_VALUES) {
+    for (size_t k = 0; k < al.size(); ++k)
+      if (std::memcmp(&al[k], &au[k], sizeof(double)) != 0) {
+        delete m;
+        return CSRC_ERR_NOT_NUM_SYMMETRIC;
+      }
+    m->sym = true;
+  }
   cudaGetDevice(&m->device);
   cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   if (m->sms <= 0) m->sms = 1;
@@ -1111,12 +1121,12 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   if ((st = from_cuda(cudaMemsetAsync(m->d_ia, 0, ((size_t)n + 1 + kMetaPad) * 4, stream))) != CSRC_OK) return fail(st);
   if (from_cuda(dmalloc(&m->d_ja, hcap)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if (cudaMalloc(&m->d_al, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
-  if (cudaMalloc(&m->d_au, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
+  if (!m->sym && cudaMalloc(&m->d_au, hcap * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if (cudaMalloc(&m->d_ad, std::max<size_t>(1, (size_t)n) * vb) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if (from_cuda(dmalloc(&m->d_status, 1)) != CSRC_OK) return fail(CSRC_ERR_OUT_OF_MEMORY);
   if ((st = from_cuda(cudaMemsetAsync(m->d_ja, 0, hcap * 4, stream))) != CSRC_OK) return fail(st);
   if ((st = from_cuda(cudaMemsetAsync(m->d_al, 0, hcap * vb, stream))) != CSRC_OK) return fail(st);
-  if ((st = from_cuda(cudaMemsetAsync(m->d_au, 0, hcap * vb, stream))) != CSRC_OK) return fail(st);
+  if (!m->sym && (st = from_cuda(cudaMemsetAsync(m->d_au, 0, hcap * vb, stream))) != CSRC_OK) return fail(st);
   if ((st = from_cuda(cudaMemsetAsync(m->d_status, 0, 4, stream))) != CSRC_OK) return fail(st);
   if ((st = from_cuda(cudaMemcpyAsync(m->d_ia, ia.data(), ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, stream))) != CSRC_OK)
     return fail(st);
@@ -1141,9 +1151,9 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
     return from_cuda(e);
   };
   if ((st = put_values(m->d_al, al)) != CSRC_OK) return fail(st);
-  if ((st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
+  if (!m->sym && (st = put_values(m->d_au, au)) != CSRC_OK) return fail(st);
   if ((st = put_values(m->d_ad, ad)) != CSRC_OK) return fail(st);
-  if (m->arith == ARITH_DF32) {
+  if (m->arith == ARITH_DF32 && !m->sym) {
     if (cudaMalloc(&m->d_al_df, hcap * 8) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
     if (cudaMalloc(&m->d_au_df, hcap * 8) != cudaSuccess) return fail(CSRC_ERR_OUT_OF_MEMORY);
     if ((st = from_cuda(launch_split_df(static_cast<const double*>(m->d_al), m->d_al_df, (int64_t)hcap, stream))) !=
@@ -1210,7 +1220,7 @@ csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row
   if (n < 0 || !row_ptr) return CSRC_ERR_INVALID_ARG;
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
-                         CSRC_FLAG_NODE_BLOCKS))
+                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1240,7 +1250,7 @@ csrc_status csrc_create_rect_from_csr(csrc_handle* out, int32_t n, int32_t m, co
   if (n < 0 || m < n || !row_ptr) return CSRC_ERR_INVALID_ARG;
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
-                         CSRC_FLAG_NODE_BLOCKS))
+                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1649,7 +1659,7 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   info->storage = h->storage;
   info->arith = h->arith;
   const int64_t vb = (int64_t)h->vbytes(), xb = (int64_t)h->xbytes();
-  info->model_bytes = 4 * ((int64_t)h->n + 1) + 4 * h->h + 2 * vb * h->h + vb * h->n + 2 * xb * h->n;
+  info->model_bytes = 4 * ((int64_t)h->n + 1) + 4 * h->h + (h->sym ? 1 : 2) * vb * h->h + vb * h->n + 2 * xb * h->n;
   if (h->have_plan) {
     info->nbands = h->plan.nb;
     info->page_rows = kPageRows;
@@ -1721,6 +1731,7 @@ const char* csrc_status_string(csrc_status st) {
     case CSRC_ERR_DEVICE_BOUNDS: return "device index check failed";
     case CSRC_ERR_RANGE: return "x value outside the double-float range";
     case CSRC_ERR_MISMATCH: return "batch members differ in storage type";
+    case CSRC_ERR_NOT_NUM_SYMMETRIC: return "symmetric-value storage requested but a_ij != a_ji";
   }
   return "unknown status";
 }

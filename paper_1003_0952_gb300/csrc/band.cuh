@@ -344,6 +344,9 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   const int st1 = a.band_stage[b + 1] - 1;  // index of the band's end entry
   const int nstages = st1 - st0;
   const int ldx = a.ldx;                    // row stride of x and y (elements)
+  // numerically symmetric storage (Section 2.2): al is also the scatter operand, so the ring
+  // carries no au (the host passes the same array for both)
+  const bool sym = a.au == a.al;
 
   // ---- shared memory: [mbarriers][ring slots][x][sums][page table][ia][stage_k][stage_r]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // full[NS], empty[NS], setup
@@ -374,10 +377,11 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
     ke = (ke + kPairAlign - 1) & ~(kPairAlign - 1);
     const int cnt = ke - ks;  // <= kStageCap + 16 (the host caps a stage's pairs)
     const uint32_t bar = bar_full + 8u * slot;
-    mbar_arrive_expect_tx(bar, (uint32_t)cnt * (uint32_t)(4 + 2 * VB));
+    mbar_arrive_expect_tx(bar, (uint32_t)cnt * (uint32_t)(4 + (sym ? 1 : 2) * VB));
     bulk_copy_g2s(smem_addr(ring_ja + (size_t)slot * SP), a.ja + ks, (uint32_t)cnt * 4u, bar);
     bulk_copy_g2s(smem_addr(ring_al + (size_t)slot * SP), static_cast<const V*>(a.al) + ks, (uint32_t)cnt * VB, bar);
-    bulk_copy_g2s(smem_addr(ring_au + (size_t)slot * SP), static_cast<const V*>(a.au) + ks, (uint32_t)cnt * VB, bar);
+    if (!sym)
+      bulk_copy_g2s(smem_addr(ring_au + (size_t)slot * SP), static_cast<const V*>(a.au) + ks, (uint32_t)cnt * VB, bar);
   };
 
   if (tid == 0) {
@@ -485,13 +489,14 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
       // stages hold whole units: this group's unit is in stage s when it starts before its end
       if (r < r1 && s_ia[r] < ke) block_unit<MODE, G, B>(r, s_ia, ring_ja + (size_t)slot * SP - (ks & ~(kPairAlign - 1)),
                                          ring_al + (size_t)slot * SP - (ks & ~(kPairAlign - 1)),
-                                         ring_au + (size_t)slot * SP - (ks & ~(kPairAlign - 1)), win, tab, plo,
+                                         (sym ? ring_al : ring_au) + (size_t)slot * SP - (ks & ~(kPairAlign - 1)),
+                                         win, tab, plo,
                                          ntab, gl, gmask, bad);
     } else if (kb < kx) {  // the whole group enters (its lanes meet in the shuffles below)
       const int base = ks & ~(kPairAlign - 1);
       const int32_t* sja = ring_ja + (size_t)slot * SP - base;
       const V* sal = ring_al + (size_t)slot * SP - base;
-      const V* sau = ring_au + (size_t)slot * SP - base;
+      const V* sau = (sym ? ring_al : ring_au) + (size_t)slot * SP - base;
       int rslot = slot_of(r);
       if (rslot < 0) {
         bad |= 4u;
@@ -530,7 +535,11 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
             const int k = k0 + u * G;
             sv[u] = min((unsigned)sja[k], smax);
             gv[u] = sal[k];
-            vv[u] = ssc[k];
+            if constexpr (MODE == MODE_DF) {
+              vv[u] = sym ? df_split<false>(gv[u], nullptr) : ssc[k];
+            } else {
+              vv[u] = sym ? gv[u] : ssc[k];
+            }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) xv[u] = win.xs[sv[u]];

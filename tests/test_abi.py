@@ -82,6 +82,20 @@ def test_host_validation_errors(cs):
     assert st == cs.CSRC_ERR_INVALID_ARG
     st, _ = _create_status(cs, 1, [0, 1], [0], [1.0], flags=1 << 10)
     assert st == cs.CSRC_ERR_INVALID_ARG
+    # symmetric-value storage requested for a matrix with a_01 != a_10
+    st, h = _create_status(cs, 2, [0, 2, 4], [0, 1, 0, 1], [1.0, 2.0, 3.0, 1.0], flags=cs.CSRC_FLAG_SYMMETRIC_VALUES)
+    assert st == cs.CSRC_ERR_NOT_NUM_SYMMETRIC and not h.value
+    # rectangular creation: fewer columns than rows, and a column past m
+    rp = np.array([0, 1, 3], np.int64)
+    col = np.array([0, 1, 2], np.int32)
+    val = np.ones(3)
+    h = ctypes.c_void_p()
+    st = cs.lib().csrc_create_rect_from_csr(ctypes.byref(h), 2, 1, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                            0, 0, None)
+    assert st == cs.CSRC_ERR_INVALID_ARG and not h.value
+    st = cs.lib().csrc_create_rect_from_csr(ctypes.byref(h), 2, 2, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                            0, 0, None)
+    assert st == cs.CSRC_ERR_INDEX_RANGE and not h.value
     # null handles and arguments
     assert cs.lib().csrc_spmv(None, None, None, 0, None) == cs.CSRC_ERR_INVALID_ARG
     assert cs.lib().csrc_partition(None, 4, None) == cs.CSRC_ERR_INVALID_ARG

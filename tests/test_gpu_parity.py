@@ -245,6 +245,80 @@ def test_symmetric_values(cs):
         h.close()
 
 
+def _symmetrised(m, seed, integer=False):
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    v = fe.hash_uniform(seed, np.minimum(rows, m.col), np.maximum(rows, m.col))
+    if integer:
+        v = np.round(v * 8.0)
+    return fe.FEMatrix(m.n, m.row_ptr, m.col, v)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_symmetric_value_storage(cs, storage):
+    # Section 2.2: au is not stored; the kernels scatter with al, and A^T x = A x
+    for base in (fe.q1_hex(9, 1, 51), fe.q1_hex(14, 3, 52)):  # 4 and 16 lanes per row
+        m = _symmetrised(base, 53)
+        x = fe.source_vector(m.n, 54)
+        if storage != "f64":
+            x = x.astype(np.float32).astype(np.float64)
+        plain = Handle(cs, m, storage)
+        h = Handle(cs, m, storage, flags=cs.CSRC_FLAG_SYMMETRIC_VALUES, seed=5)
+        mi = _symmetrised(base, 55, integer=True)
+        xi = fe.integer_vector(m.n, 56)
+        hi = Handle(cs, mi, storage, flags=cs.CSRC_FLAG_SYMMETRIC_VALUES, seed=6)
+        try:
+            for strategy in STRATS:
+                for tr in (False, True):
+                    _check(m, x, h.run(x, strategy, tr), tr, TOL[storage])
+                    np.testing.assert_array_equal(hi.run(xi, strategy, tr), _ref(mi, xi, tr))
+            plain.run(x)
+            ip, ih = cs.csrc_get_info(plain.h), cs.csrc_get_info(h.h)
+            vb = {"f64": 8, "f32": 4, "bf16": 2}[storage]
+            assert ip["model_bytes"] - ih["model_bytes"] == vb * ip["pairs"]
+        finally:
+            plain.close()
+            h.close()
+            hi.close()
+
+
+def test_symmetric_value_storage_other_paths(cs):
+    # node blocks, several right-hand sides and the batched graph read al as the scatter operand too
+    m = _symmetrised(fe.q1_hex(8, 3, 57), 58)
+    c = oracle.from_matrix(m)
+    flags = cs.CSRC_FLAG_SYMMETRIC_VALUES
+    h = Handle(cs, m, flags=flags | cs.CSRC_FLAG_NODE_BLOCKS)
+    try:
+        x = fe.source_vector(m.n, 59)
+        _check(m, x, h.run(x, "window", False), False, TOL["f64"])
+        assert cs.csrc_get_info(h.h)["block"] == 3
+    finally:
+        h.close()
+    h = Handle(cs, m, flags=flags)
+    try:
+        X = fe.source_vector(m.n, 60, nrhs=4)
+        Xd = torch.as_tensor(X).cuda()
+        Yd = torch.full_like(Xd, float("nan"))
+        cs.csrc_spmm_batched([h.h], [Xd], [Yd], 4, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert oracle.max_rel_err(m, X, Yd.cpu().numpy(), oracle.csrc_spmm(c, X)) <= TOL["f64"]
+    finally:
+        h.close()
+    mats = [_symmetrised(fe.p1_grid(30 + 5 * i, 20, 61 + i), 62 + i) for i in range(3)]
+    hs = [cs.csrc_create_from_csr(q.n, q.row_ptr, q.col, q.val, cs.CSRC_F32, flags) for q in mats]
+    try:
+        xs = [fe.source_vector(q.n, 70 + i).astype(np.float32).astype(np.float64) for i, q in enumerate(mats)]
+        Xd = [torch.as_tensor(v, dtype=torch.float32).cuda() for v in xs]
+        Yd = [torch.full_like(v, float("nan")) for v in Xd]
+        cs.csrc_spmm_batched(hs, Xd, Yd, 1, False, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for q, v, y in zip(mats, xs, Yd):
+            ref = oracle.csrc_spmv(oracle.from_matrix(q), v)
+            assert oracle.max_rel_err(q, v, y.cpu().numpy().astype(np.float64), ref) <= TOL["f32"]
+    finally:
+        for hh in hs:
+            cs.csrc_destroy(hh)
+
+
 # --------------------------------------------------------------------------- interface behaviour
 def test_host_pointers_are_staged(cs):
     m = fe.p1_grid(50, 40, 9)
