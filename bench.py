@@ -444,7 +444,7 @@ def run_suite(args):
             finally:
                 cs.csrc_destroy(h)
 
-    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1"}
+    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2"}
     if "c1" in sel:
         m, _ = build_workload("p1_100x100")
         spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
@@ -511,6 +511,27 @@ def run_suite(args):
         finally:
             cs.csrc_destroy(h)
         del a
+    if "n2" in sel:
+        # numerically symmetric storage (Section 2.2): q1v_96's pattern with a_ji = a_ij, au not stored
+        g, _ = build_workload("q1v_96")
+        rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+        g.val = fe.hash_uniform(1006, np.minimum(rows, g.col), np.maximum(rows, g.col))
+        del rows
+        h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.CSRC_F64, cs.CSRC_FLAG_SYMMETRIC_VALUES)
+        try:
+            cs.csrc_partition(h, 0)
+            x = torch.from_numpy(fe.source_vector(g.n, 12)).cuda()
+            y = torch.empty_like(x)
+            mb = cs.csrc_get_info(h)["model_bytes"]  # 6 nnz + 22 n + 4
+            ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+            emit({"suite": "N2 numerically symmetric CSRC (au not stored): q1v_96 pattern", "n": g.n, "nnz": g.nnz,
+                  "storage": "f64", "strategy": "window", "ms_per_product": ms, "model_bytes": mb,
+                  "GB/s": mb / ms / 1e6, "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6})
+            if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
+                raise RuntimeError("device status")
+        finally:
+            cs.csrc_destroy(h)
+        del g
     if "c5" in sel:
         ms_list = fe.batch_meshes(256, 1005)
         tot_n = sum(m.n for m in ms_list)
@@ -562,7 +583,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", default=None,
-                    help="all, or a comma list of c1..c5, n1: one JSON line per configuration row")
+                    help="all, or a comma list of c1..c5, n1, n2: one JSON line per configuration row")
     ap.add_argument("--suite-iters", type=int, default=20)
     ap.add_argument("--tet-method", default="delaunay", choices=["delaunay", "kuhn"])
     args = ap.parse_args(argv)
