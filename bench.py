@@ -444,7 +444,7 @@ def run_suite(args):
             finally:
                 cs.csrc_destroy(h)
 
-    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2"}
+    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2", "n3"}
     if "c1" in sel:
         m, _ = build_workload("p1_100x100")
         spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
@@ -532,6 +532,28 @@ def run_suite(args):
         finally:
             cs.csrc_destroy(h)
         del g
+    if "n3" in sel:
+        # index compression: 16-bit band-local window slots instead of 32-bit ones, q1v_96
+        g, _ = build_workload("q1v_96")
+        xs = fe.source_vector(g.n, 13)
+        for storage in ("f64", "bf16"):
+            for flags, label in ((0, "32-bit slots"), (cs.CSRC_FLAG_COMPRESS_INDICES, "16-bit slots")):
+                h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.STORAGE[storage], flags)
+                try:
+                    cs.csrc_partition(h, 0)
+                    dt = torch.float64 if storage == "f64" else torch.float32
+                    x = torch.from_numpy(xs).to(dt).cuda()
+                    y = torch.empty_like(x)
+                    mb = cs.csrc_get_info(h)["model_bytes"]
+                    ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+                    emit({"suite": "N3 index compression: q1v_96", "storage": storage, "indices": label,
+                          "ms_per_product": ms, "model_bytes": mb, "GB/s": mb / ms / 1e6,
+                          "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6})
+                    if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
+                        raise RuntimeError("device status")
+                finally:
+                    cs.csrc_destroy(h)
+        del g
     if "c5" in sel:
         ms_list = fe.batch_meshes(256, 1005)
         tot_n = sum(m.n for m in ms_list)
@@ -583,7 +605,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", default=None,
-                    help="all, or a comma list of c1..c5, n1, n2: one JSON line per configuration row")
+                    help="all, or a comma list of c1..c5, n1..n3: one JSON line per configuration row")
     ap.add_argument("--suite-iters", type=int, default=20)
     ap.add_argument("--tet-method", default="delaunay", choices=["delaunay", "kuhn"])
     args = ap.parse_args(argv)

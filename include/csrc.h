@@ -83,6 +83,11 @@ enum {
                                      bit for bit (checked at creation), au is not stored and the
                                      kernels scatter with al, so a product streams 12 instead of 20
                                      bytes per pair in FP64; A^T x = A x */
+  CSRC_FLAG_COMPRESS_INDICES = 32, /* the window strategy's single-vector plans keep each pair's band-local
+                                     window slot as 16 bits (index compression): a product streams 2
+                                     instead of 4 index bytes per pair (18 / 10 / 6 bytes per pair in
+                                     FP64 / FP32 / BF16); a plan whose windows exceed 65,536 rows keeps
+                                     32-bit slots */
   CSRC_FLAG_NODE_BLOCKS = 8  /* when the matrix has node blocks (B = 2 or 3 consecutive rows sharing
                                 their columns, as with B unknowns per FE node), run node-block units */
 };

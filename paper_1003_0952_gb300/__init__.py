@@ -42,6 +42,7 @@ CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC = 0, 1, 
 # flags
 CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH, CSRC_FLAG_NODE_BLOCKS = 1, 2, 4, 8
 CSRC_FLAG_SYMMETRIC_VALUES = 16
+CSRC_FLAG_COMPRESS_INDICES = 32
 
 STRATEGIES = {"auto": CSRC_STRAT_AUTO, "window": CSRC_STRAT_WINDOW, "color": CSRC_STRAT_COLOR,
               "atomic": CSRC_STRAT_ATOMIC}

@@ -128,7 +128,7 @@ void free_plan(DevPlan& p) {
   dfree(p.band_row); dfree(p.band_plo); dfree(p.band_ntab); dfree(p.band_wp);
   dfree(p.wpage); dfree(p.wbase); dfree(p.wmask);
   dfree(p.acc_row); dfree(p.acc_ptr); dfree(p.acc_src); dfree(p.spill_buf);
-  dfree(p.band_stage); dfree(p.stage_k); dfree(p.stage_r); dfree(p.jslot);
+  dfree(p.band_stage); dfree(p.stage_k); dfree(p.stage_r); dfree(p.jslot); dfree(p.jslot16);
   p = DevPlan();
 }
 
@@ -475,7 +475,16 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
         jslot[(size_t)k] = q < 0 ? 0 : (q << kPageShift) | (j & (kPageRows - 1));
       }
     }
-    CSRC_TRY(upload(&p.jslot, jslot, s));
+    bool narrow = (h->flags & CSRC_FLAG_COMPRESS_INDICES) != 0;
+    for (size_t b = 0; narrow && b + 1 < hp.band_row.size(); ++b)
+      narrow = (int64_t)(hp.band_wp[b + 1] - hp.band_wp[b]) * kPageRows <= 65536;
+    if (narrow) {
+      std::vector<uint16_t> j16(jslot.size());
+      for (size_t k = 0; k < jslot.size(); ++k) j16[k] = (uint16_t)jslot[k];
+      CSRC_TRY(upload(&p.jslot16, j16, s));
+    } else {
+      CSRC_TRY(upload(&p.jslot, jslot, s));
+    }
   }
   CSRC_TRY(cudaStreamSynchronize(s));
   p.spill = hp.spill;
@@ -625,7 +634,8 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
   const bool local = !atomic && rk == 1 && p.block == 1;
   a.n = h->n;
   a.ia = h->d_ia;
-  a.ja = local ? p.jslot : h->d_ja;
+  a.ja = local && p.jslot ? p.jslot : h->d_ja;
+  a.ja16 = local ? p.jslot16 : nullptr;
   a.band_stage = p.band_stage;
   a.stage_k = p.stage_k;
   a.stage_r = p.stage_r;
@@ -1220,7 +1230,8 @@ csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row
   if (n < 0 || !row_ptr) return CSRC_ERR_INVALID_ARG;
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
-                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES))
+                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES |
+                         CSRC_FLAG_COMPRESS_INDICES))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1250,7 +1261,8 @@ csrc_status csrc_create_rect_from_csr(csrc_handle* out, int32_t n, int32_t m, co
   if (n < 0 || m < n || !row_ptr) return CSRC_ERR_INVALID_ARG;
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
-                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES))
+                         CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES |
+                         CSRC_FLAG_COMPRESS_INDICES))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1659,7 +1671,8 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   info->storage = h->storage;
   info->arith = h->arith;
   const int64_t vb = (int64_t)h->vbytes(), xb = (int64_t)h->xbytes();
-  info->model_bytes = 4 * ((int64_t)h->n + 1) + 4 * h->h + (h->sym ? 1 : 2) * vb * h->h + vb * h->n + 2 * xb * h->n;
+  const int64_t ib = h->have_plan && h->plan.jslot16 ? 2 : 4;  // index bytes per pair
+  info->model_bytes = 4 * ((int64_t)h->n + 1) + ib * h->h + (h->sym ? 1 : 2) * vb * h->h + vb * h->n + 2 * xb * h->n;
   if (h->have_plan) {
     info->nbands = h->plan.nb;
     info->page_rows = kPageRows;

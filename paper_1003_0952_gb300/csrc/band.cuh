@@ -377,8 +377,12 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
     ke = (ke + kPairAlign - 1) & ~(kPairAlign - 1);
     const int cnt = ke - ks;  // <= kStageCap + 16 (the host caps a stage's pairs)
     const uint32_t bar = bar_full + 8u * slot;
-    mbar_arrive_expect_tx(bar, (uint32_t)cnt * (uint32_t)(4 + (sym ? 1 : 2) * VB));
-    bulk_copy_g2s(smem_addr(ring_ja + (size_t)slot * SP), a.ja + ks, (uint32_t)cnt * 4u, bar);
+    const uint32_t ib = a.ja16 ? 2u : 4u;  // index bytes per pair
+    mbar_arrive_expect_tx(bar, (uint32_t)cnt * (ib + (uint32_t)((sym ? 1 : 2) * VB)));
+    if (a.ja16)
+      bulk_copy_g2s(smem_addr(ring_ja + (size_t)slot * SP), a.ja16 + ks, (uint32_t)cnt * 2u, bar);
+    else
+      bulk_copy_g2s(smem_addr(ring_ja + (size_t)slot * SP), a.ja + ks, (uint32_t)cnt * 4u, bar);
     bulk_copy_g2s(smem_addr(ring_al + (size_t)slot * SP), static_cast<const V*>(a.al) + ks, (uint32_t)cnt * VB, bar);
     if (!sym)
       bulk_copy_g2s(smem_addr(ring_au + (size_t)slot * SP), static_cast<const V*>(a.au) + ks, (uint32_t)cnt * VB, bar);
@@ -525,6 +529,8 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
         constexpr int U = G == 16 ? 3 : 4;
         const unsigned smax = (unsigned)(nslots - 1);
         const SV* ssc = reinterpret_cast<const SV*>(ring_au + (size_t)slot * SP) - (ks & ~(kPairAlign - 1));
+        const uint16_t* s16 = reinterpret_cast<const uint16_t*>(ring_ja + (size_t)slot * SP) - (ks & ~(kPairAlign - 1));
+        const bool narrow = a.ja16 != nullptr;
         for (int k0 = kb + gl; k0 < kx; k0 += U * G) {
           unsigned sv[U];
           V gv[U];
@@ -533,7 +539,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int k = k0 + u * G;
-            sv[u] = min((unsigned)sja[k], smax);
+            sv[u] = min(narrow ? (unsigned)s16[k] : (unsigned)sja[k], smax);
             gv[u] = sal[k];
             if constexpr (MODE == MODE_DF) {
               vv[u] = sym ? df_split<false>(gv[u], nullptr) : ssc[k];

@@ -146,6 +146,7 @@ struct DevPlan {
   // single-vector plans of plain rows: the window slot of every stored pair, written in
   // place of its column for the window strategy (h entries, padded like ja)
   int32_t* jslot = nullptr;
+  uint16_t* jslot16 = nullptr;   // the same slots as 16 bits (index compression); jslot is then null
 };
 
 // Arguments of the band kernels (passed by value).
@@ -154,6 +155,8 @@ struct BandArgs {
   const int32_t* ia;
   const int32_t* ja;  // columns; window slots (DevPlan::jslot) for the window strategy's
                       // single-vector plain-row kernels
+  const uint16_t* ja16;  // 16-bit window slots in place of ja for those kernels (index
+                         // compression), else null
   const int32_t* band_stage;
   const int32_t* stage_k;
   const int32_t* stage_r;

@@ -319,6 +319,35 @@ def test_symmetric_value_storage_other_paths(cs):
             cs.csrc_destroy(hh)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_index_compression(cs, storage):
+    # 16-bit band-local window slots in place of 32-bit ones (the window strategy's plans)
+    for base in (fe.q1_hex(9, 1, 81), fe.q1_hex(14, 3, 82)):
+        x = fe.source_vector(base.n, 83)
+        if storage != "f64":
+            x = x.astype(np.float32).astype(np.float64)
+        mi = fe.FEMatrix(base.n, base.row_ptr, base.col, fe.integer_values(base.row_ptr, base.col, 84))
+        xi = fe.integer_vector(base.n, 85)
+        plain = Handle(cs, base, storage)
+        h = Handle(cs, base, storage, flags=cs.CSRC_FLAG_COMPRESS_INDICES, seed=7)
+        hi = Handle(cs, mi, storage, flags=cs.CSRC_FLAG_COMPRESS_INDICES, seed=8)
+        ms = _symmetrised(base, 86)
+        hs = Handle(cs, ms, storage, flags=cs.CSRC_FLAG_COMPRESS_INDICES | cs.CSRC_FLAG_SYMMETRIC_VALUES)
+        try:
+            for nbands in (None, 9):
+                for strategy in STRATS:
+                    for tr in (False, True):
+                        _check(base, x, h.run(x, strategy, tr, nbands=nbands), tr, TOL[storage])
+                        np.testing.assert_array_equal(hi.run(xi, strategy, tr, nbands=nbands), _ref(mi, xi, tr))
+                _check(ms, x, hs.run(x, "window", False, nbands=nbands), False, TOL[storage])
+            plain.run(x)
+            ip, ih = cs.csrc_get_info(plain.h), cs.csrc_get_info(h.h)
+            assert ip["model_bytes"] - ih["model_bytes"] == 2 * ip["pairs"]
+        finally:
+            for hh in (plain, h, hi, hs):
+                hh.close()
+
+
 # --------------------------------------------------------------------------- interface behaviour
 def test_host_pointers_are_staged(cs):
     m = fe.p1_grid(50, 40, 9)
