@@ -286,6 +286,66 @@ def test_rectangular_error_metric_and_rejections():
         oracle.csr_to_csrcr(a.n, a.n - 1, a.row_ptr, a.col, a.val)
 
 
+# --------------------------------------------------------------------------- BiCG (Section 1's oblique-projection solvers)
+@pytest.mark.parametrize("n,density,seed", [(5, 0.5, 91), (40, 0.2, 92), (120, 0.05, 93)])
+def test_bicg_solves_against_dense_direct_solution(n, density, seed):
+    m = _random_matrix(n, density, seed, empty_rows=False)  # diagonally dominant (ad = 1 + sum |a|)
+    c = oracle.from_matrix(m)
+    xt = fe.source_vector(n, seed + 1)
+    b = oracle.dense_spmv(n, m.row_ptr, m.col, m.val, xt)
+    res = oracle.bicg(c, b, rtol=1e-13, maxit=10 * n)
+    assert res.status == "converged"
+    a = np.zeros((n, n))
+    for i in range(n):
+        a[i, m.col[m.row_ptr[i]:m.row_ptr[i + 1]]] = m.val[m.row_ptr[i]:m.row_ptr[i + 1]]
+    np.testing.assert_allclose(res.x, np.linalg.solve(a, b), rtol=1e-9, atol=1e-11)
+    # the true residual (CSR product, Section 1) meets the tolerance up to the rounding drift of
+    # the recursively updated one
+    r = b - oracle.csr_spmv(n, m.row_ptr, m.col, m.val, res.x)
+    assert np.linalg.norm(r) <= max(1e-13, res.relres) * 10.0 * np.linalg.norm(b)
+
+
+def test_bicg_on_symmetric_spd_matches_conjugate_gradients():
+    # with a = a^T and r*_0 = r_0 BiCG's iterates are those of CG (Saad, Section 7.3.1)
+    rp, c = fe.q1_hex27_pattern(6, 6, 6)
+    n = len(rp) - 1
+    m = fe.FEMatrix(n, rp, c, fe.laplacian_values(rp, c) + 0.0)
+    diag = np.repeat(np.arange(n), np.diff(rp)) == c
+    m.val[diag] += 1.0  # 27-point Laplacian plus identity: SPD
+    cc = oracle.from_matrix(m)
+    b = fe.source_vector(n, 94)
+    res = oracle.bicg(cc, b, rtol=1e-12, maxit=500)
+    # plain CG written out here with scipy's sparse product (an independent product)
+    a = sp.csr_matrix((m.val, m.col, m.row_ptr), shape=(n, n))
+    x = np.zeros(n)
+    r = b.copy()
+    p = r.copy()
+    rr = r @ r
+    it = 0
+    while np.sqrt(rr) > 1e-12 * np.linalg.norm(b):
+        q = a @ p
+        al = rr / (p @ q)
+        x += al * p
+        r -= al * q
+        rr2 = r @ r
+        p = r + (rr2 / rr) * p
+        rr = rr2
+        it += 1
+    assert res.status == "converged"
+    assert abs(res.iters - it) <= 1
+    np.testing.assert_allclose(res.x, x, rtol=1e-9, atol=1e-12)
+
+
+def test_bicg_reports_maxit_and_zero_rhs():
+    m = _random_matrix(30, 0.2, 95, empty_rows=False)
+    c = oracle.from_matrix(m)
+    b = fe.source_vector(30, 96)
+    res = oracle.bicg(c, b, rtol=1e-14, maxit=2)
+    assert res.status == "maxit" and res.iters == 2 and res.relres > 1e-14
+    res = oracle.bicg(c, np.zeros(30), rtol=1e-10)
+    assert res.status == "converged" and res.iters == 0 and np.all(res.x == 0)
+
+
 def test_spmm_columns_match_dense():
     m = _random_matrix(30, 0.2, 21)
     c = oracle.from_matrix(m)
