@@ -444,7 +444,7 @@ def run_suite(args):
             finally:
                 cs.csrc_destroy(h)
 
-    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2", "n3"}
+    sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2", "n3", "n4"}
     if "c1" in sel:
         m, _ = build_workload("p1_100x100")
         spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
@@ -554,6 +554,30 @@ def run_suite(args):
                 finally:
                     cs.csrc_destroy(h)
         del g
+    if "n4" in sel:
+        # BiCG (csrc_bicg) on q1v_96: one A p and one A^T p* per iteration plus two vector passes
+        g, _ = build_workload("q1v_96")
+        h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.CSRC_F64)
+        try:
+            cs.csrc_partition(h, 0)
+            b = torch.from_numpy(fe.source_vector(g.n, 14)).cuda()
+            x = torch.zeros_like(b)
+            cs.csrc_bicg(h, b, x, 1e-8, 3)  # warm-up (plans, scratch)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = cs.csrc_bicg(h, b, x, 1e-8, 500)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3
+            it = max(res["iters"], 1)
+            # per iteration: two products (model bytes each) and 19 n vector reads/writes of 8 bytes
+            per_it = 2 * cs.csrc_get_info(h)["model_bytes"] + 19 * 8 * g.n
+            emit({"suite": "N4 BiCG on q1v_96 (csrc_bicg, FP64, window)", "status": res["status"],
+                  "iters": res["iters"], "relres": res["relres"], "ms_total_host_clock": ms,
+                  "ms_per_iteration": ms / it, "GB/s": per_it * it / ms / 1e6})
+        finally:
+            cs.csrc_destroy(h)
+        del g
     if "c5" in sel:
         ms_list = fe.batch_meshes(256, 1005)
         tot_n = sum(m.n for m in ms_list)
@@ -605,7 +629,7 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", default=None,
-                    help="all, or a comma list of c1..c5, n1..n3: one JSON line per configuration row")
+                    help="all, or a comma list of c1..c5, n1..n4: one JSON line per configuration row")
     ap.add_argument("--suite-iters", type=int, default=20)
     ap.add_argument("--tet-method", default="delaunay", choices=["delaunay", "kuhn"])
     args = ap.parse_args(argv)

@@ -62,7 +62,9 @@ typedef enum {
   CSRC_ERR_DEVICE_BOUNDS = 11,       /* a device-side index check failed (device status word) */
   CSRC_ERR_RANGE = 12,               /* an x value lies outside the double-float range (device status word) */
   CSRC_ERR_MISMATCH = 13,            /* batch members differ in storage type */
-  CSRC_ERR_NOT_NUM_SYMMETRIC = 14    /* CSRC_FLAG_SYMMETRIC_VALUES set but some a_ij != a_ji */
+  CSRC_ERR_NOT_NUM_SYMMETRIC = 14,   /* CSRC_FLAG_SYMMETRIC_VALUES set but some a_ij != a_ji */
+  CSRC_ERR_NOT_CONVERGED = 15,       /* csrc_bicg reached maxit above the tolerance (x = last iterate) */
+  CSRC_ERR_BREAKDOWN = 16            /* csrc_bicg met (r, r*) = 0 or (A p, p*) = 0 (x = last iterate) */
 } csrc_status;
 
 typedef enum { CSRC_F64 = 0, CSRC_F32 = 1, CSRC_BF16 = 2 } csrc_dtype; /* storage of ad, al, au */
@@ -295,6 +297,27 @@ csrc_status csrc_set_profiling(csrc_handle h, int32_t enable);
  * *out (host), and drop the records. Errors: INVALID_ARG, CUDA.
  */
 csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out);
+
+/*
+ * Solve A x = b by biconjugate gradients (BiCG: Fletcher's method as in Saad, Iterative
+ * Methods for Sparse Linear Systems, 2nd ed., Algorithm 7.3, shadow residual r*_0 = r_0):
+ * the oblique-projection solver that Section 1 names as a user of CSRC's implicit
+ * transpose. Every iteration runs one csrc_spmv (A p) and one csrc_spmv_t (A^T p*) with
+ * the given strategy, and two fused vector passes on the device; inner products are
+ * summed in FP64 in a fixed order (deterministic). Stops when ||r||_2 <= rtol ||b||_2 for
+ * the recursively updated residual r.
+ *   b, x      device vectors of n elements of the handle's vector type (double for
+ *             CSRC_F64, float otherwise); x holds the initial guess and receives the solution
+ *   rtol      relative tolerance (>= 0); maxit iterations at most (>= 0)
+ *   iters_out, relres_out  optional host outputs: iterations run and ||r||_2 / ||b||_2
+ *             (0 when b = 0)
+ * Square handles only. Synchronises the stream every iteration (the scalars go to the
+ * host). The handle keeps six scratch vectors for later calls.
+ * Errors: INVALID_ARG, ALIAS, NOT_PARTITIONED, NOT_COLORED, OUT_OF_MEMORY, CUDA, and
+ * NOT_CONVERGED / BREAKDOWN (outputs and x still set).
+ */
+csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_t maxit, csrc_strategy strategy,
+                      int32_t* iters_out, double* relres_out, cudaStream_t stream);
 
 /* Fill *info (host). */
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info);

@@ -34,6 +34,8 @@ CSRC_ERR_DEVICE_BOUNDS = 11
 CSRC_ERR_RANGE = 12
 CSRC_ERR_MISMATCH = 13
 CSRC_ERR_NOT_NUM_SYMMETRIC = 14
+CSRC_ERR_NOT_CONVERGED = 15
+CSRC_ERR_BREAKDOWN = 16
 
 # storage (csrc_dtype)
 CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
@@ -89,6 +91,8 @@ SIGNATURES = {
     "csrc_create_rect_from_csr": (ctypes.c_int, [_P(_VP), ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int,
                                                  ctypes.c_uint32, _VP]),
     "csrc_partition": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
+    "csrc_bicg": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, _P(ctypes.c_int32),
+                                 _P(ctypes.c_double), _VP]),
     "csrc_color": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(ctypes.c_int32), _VP]),
     "csrc_spmv": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "csrc_spmv_t": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -231,6 +235,19 @@ CSRC_NOALLOC_MAX_SPILL_ENTRIES = 1 << 21
 def csrc_spmv_noalloc(h, x, y, transpose=False, stream=None) -> None:
     """Window-strategy product that allocates nothing (spill in the library's static array)."""
     _check(_lib.csrc_spmv_noalloc(h, _ptr(x), _ptr(y), int(bool(transpose)), _stream(stream)), "csrc_spmv_noalloc")
+
+
+def csrc_bicg(h, b, x, rtol=1e-10, maxit=1000, strategy=CSRC_STRAT_AUTO, stream=None) -> dict:
+    """Solve A x = b by BiCG on the device (x: initial guess in, solution out). Returns
+    {"status", "iters", "relres"}; NOT_CONVERGED and BREAKDOWN are reported there, other
+    errors raise CsrcError."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = _lib.csrc_bicg(h, _ptr(b), _ptr(x), float(rtol), int(maxit), int(strategy), ctypes.byref(it),
+                        ctypes.byref(rr), _stream(stream))
+    if st not in (CSRC_OK, CSRC_ERR_NOT_CONVERGED, CSRC_ERR_BREAKDOWN):
+        _check(st, "csrc_bicg")
+    return {"status": st, "iters": it.value, "relres": rr.value}
 
 
 def csrc_autotune(h, x, y, stream=None) -> None:

@@ -48,6 +48,9 @@ struct csrc_matrix_s {
   int32_t* d_rptr = nullptr;
   int32_t* d_rcol = nullptr;
   void* d_rval = nullptr;
+  // BiCG scratch (csrc_bicg): r, r*, p, p*, q, q* and the partial inner products
+  void* d_solve = nullptr;
+  double* d_partial = nullptr;
   int32_t* d_tptr = nullptr;
   int32_t* d_trow = nullptr;
   void* d_tval = nullptr;
@@ -1662,6 +1665,69 @@ csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out) {
   return st;
 }
 
+csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_t maxit, csrc_strategy strategy,
+                      int32_t* iters_out, double* relres_out, cudaStream_t stream) {
+  if (iters_out) *iters_out = 0;
+  if (relres_out) *relres_out = 0.0;
+  if (!h || !b || !x || !(rtol >= 0.0) || maxit < 0 || h->rect()) return CSRC_ERR_INVALID_ARG;
+  if (!is_device_ptr(b) || !is_device_ptr(x)) return CSRC_ERR_INVALID_ARG;
+  const int64_t n = h->n;
+  const size_t vb = (size_t)n * h->xbytes();
+  const char* ba = static_cast<const char*>(b);
+  const char* xa = static_cast<const char*>(x);
+  if (ba < xa + vb && xa < ba + vb) return CSRC_ERR_ALIAS;
+  if (n == 0) return CSRC_OK;
+  CSRC_TRY_S(ensure_device(h));
+  const bool fp64 = h->xbytes() == 8;
+  const int nb = solver_blocks(h->sms);
+  if (!h->d_solve) CSRC_TRY(cudaMalloc(&h->d_solve, 6 * vb));
+  if (!h->d_partial) CSRC_TRY(dmalloc(&h->d_partial, (size_t)2 * nb + 2));
+  char* base = static_cast<char*>(h->d_solve);
+  void *r = base, *rs = base + vb, *p = base + 2 * vb, *ps = base + 3 * vb, *q = base + 4 * vb, *qs = base + 5 * vb;
+  double* out = h->d_partial + 2 * nb;
+  double hv[2] = {0.0, 0.0};
+  auto pass = [&](int op, double sc, const void* v0, const void* v1, const void* v2, void* w0, void* w1, void* w2,
+                  void* w3) -> csrc_status {
+    CSRC_TRY(timed_launch(h, CSRC_KERNEL_OTHER, stream, [&] {
+      return launch_solver_op(op, fp64, n, nb, sc, v0, v1, v2, w0, w1, w2, w3, h->d_partial, out, stream);
+    }, op == SOLVER_UPDATE2 ? 1 : 2));
+    if (op != SOLVER_UPDATE2) {
+      CSRC_TRY(cudaMemcpyAsync(hv, out, (op == SOLVER_DOT ? 1 : 2) * sizeof(double), cudaMemcpyDeviceToHost, stream));
+      CSRC_TRY(cudaStreamSynchronize(stream));
+    }
+    return CSRC_OK;
+  };
+  // r = b - A x; r* = p = p* = r
+  CSRC_TRY_S(run_spmv(h, x, q, strategy, stream, false));
+  CSRC_TRY_S(pass(SOLVER_INIT, 0.0, b, q, nullptr, r, rs, p, ps));
+  double nrm2 = hv[0];
+  const double bb = hv[1];
+  const double tol2 = rtol * rtol * bb;
+  double rho = nrm2;  // (r, r*) with r* = r
+  auto finish = [&](int32_t it, csrc_status st) {
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = bb > 0.0 ? std::sqrt(nrm2 / bb) : 0.0;
+    return st;
+  };
+  if (nrm2 <= tol2) return finish(0, CSRC_OK);
+  for (int32_t it = 1; it <= maxit; ++it) {
+    CSRC_TRY_S(run_spmv(h, p, q, strategy, stream, false));
+    CSRC_TRY_S(run_spmv(h, ps, qs, strategy, stream, true));
+    CSRC_TRY_S(pass(SOLVER_DOT, 0.0, q, ps, nullptr, nullptr, nullptr, nullptr, nullptr));
+    const double sigma = hv[0];
+    if (rho == 0.0 || sigma == 0.0 || !std::isfinite(sigma)) return finish(it - 1, CSRC_ERR_BREAKDOWN);
+    const double alpha = rho / sigma;
+    CSRC_TRY_S(pass(SOLVER_UPDATE1, alpha, p, q, qs, x, r, rs, nullptr));
+    nrm2 = hv[0];
+    if (nrm2 <= tol2) return finish(it, CSRC_OK);
+    const double rho_new = hv[1];
+    const double beta = rho_new / rho;
+    rho = rho_new;
+    CSRC_TRY_S(pass(SOLVER_UPDATE2, beta, r, rs, nullptr, p, ps, nullptr, nullptr));
+  }
+  return finish(maxit, CSRC_ERR_NOT_CONVERGED);
+}
+
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   if (!h || !info) return CSRC_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));
@@ -1721,6 +1787,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   dfree(h->d_al_df); dfree(h->d_au_df);
   dfree(h->d_rrow); dfree(h->d_rptr); dfree(h->d_rcol); dfree(h->d_rval);
   dfree(h->d_tptr); dfree(h->d_trow); dfree(h->d_tval);
+  dfree(h->d_solve); dfree(h->d_partial);
   dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
   release_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
@@ -1745,6 +1812,8 @@ const char* csrc_status_string(csrc_status st) {
     case CSRC_ERR_RANGE: return "x value outside the double-float range";
     case CSRC_ERR_MISMATCH: return "batch members differ in storage type";
     case CSRC_ERR_NOT_NUM_SYMMETRIC: return "symmetric-value storage requested but a_ij != a_ji";
+    case CSRC_ERR_NOT_CONVERGED: return "iteration limit reached above the tolerance";
+    case CSRC_ERR_BREAKDOWN: return "BiCG breakdown: a zero inner product";
   }
   return "unknown status";
 }

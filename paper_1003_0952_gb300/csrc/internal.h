@@ -211,6 +211,16 @@ cudaError_t launch_rect_rows(int storage, int32_t nrows, const int32_t* rows, co
                              const void* val, const void* x, void* y, cudaStream_t s);
 cudaError_t launch_rect_cols(int storage, int32_t ncols, int32_t n, const int32_t* ptr, const int32_t* row,
                              const void* val, const void* x, void* y, cudaStream_t s);
+// Vector passes of the BiCG solver (solver.cu). SOLVER_DOT: out[0] = (v0, v1).
+// SOLVER_INIT: w0 = w1 = w2 = w3 = v0 - v1, out = {(w0, w0), (v0, v0)}.
+// SOLVER_UPDATE1: w0 += s v0; w1 -= s v1; w2 -= s v2; out = {(w1, w1), (w1, w2)}.
+// SOLVER_UPDATE2: w0 = v0 + s w0; w1 = v1 + s w1. Vectors of n doubles (fp64) or floats;
+// partial holds 2 * nblocks doubles, out 2; sums are FP64 and in a fixed order.
+enum SolverOp : int { SOLVER_DOT = 0, SOLVER_INIT = 1, SOLVER_UPDATE1 = 2, SOLVER_UPDATE2 = 3 };
+int solver_blocks(int sms);
+cudaError_t launch_solver_op(int op, bool fp64, int64_t n, int nblocks, double scalar, const void* v0, const void* v1,
+                             const void* v2, void* w0, void* w1, void* w2, void* w3, double* partial, double* out,
+                             cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
 cudaError_t prepare_band_kernels_block();
