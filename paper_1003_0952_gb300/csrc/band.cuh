@@ -467,14 +467,14 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   };
 
   // ---- phase 2: stream the band's pairs, one row per group of G lanes. The groups of a
-  // warp take rows D apart: warp w's groups g take rows (w / D) * D * GPW + g * D + w % D.
-  // Long rows (G >= 8, up to 3-DOF node rows whose neighbours share targets) spread as far
-  // as possible (D = W, rows g * W + w), so the lanes of one warp rarely hit the same window
-  // slot. Short rows (G <= 4) stay close (D = G): their ring slices, x entries and window
-  // slots then fall on nearby addresses, which measured 15-57 % faster (Q1 scalar, P1 and
-  // tetrahedral meshes).
+  // warp take rows D = G apart: warp w's groups g take rows (w / G) * 32 + g * G + w % G, so
+  // the 32 rows that warps w0..w0+G-1 share form one block of consecutive rows. Their ring
+  // slices, x entries and window slots fall on nearby addresses while a warp's rows stay far
+  // enough apart not to share a node (and its targets) in 3-DOF meshes. Measured against
+  // spreading rows one warp apart (rows g * W + w): band kernel 15-57 % faster for 1-4 lanes
+  // per row (Q1 scalar, P1 and tetrahedral meshes), 7-10 % for q1v_96 (16 lanes).
   constexpr int W = T / 32, GPW = 32 / G;
-  constexpr int D = G <= 4 ? G : W;
+  constexpr int D = G;
   static_assert(W % D == 0, "the row spacing divides the warp count");
   const int rowoff = (warp / D) * (D * GPW) + ((lane / G) % GPW) * D + (warp % D);
   const int gl = lane % G;  // lane within the group
