@@ -70,6 +70,11 @@ struct csrc_matrix_s {
   DevPlan plan_b1;            // plain-row plan when the main plan uses node blocks
   bool have_b1 = false;
   bool covers_b1 = false;
+  // plan of the batched kernel: bands sized by non-zeros alone (the batch's other members fill
+  // the GPU), built on first use; the matrix never changes, so it is kept until destroy
+  DevPlan plan_bt;
+  bool have_bt = false;
+  bool covers_bt = false;
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -548,6 +553,24 @@ csrc_status plan_b1_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
   return CSRC_OK;
 }
 
+// The plan of a batch member: plain rows, about kBatchBandNnz non-zeros per band before
+// windows are fitted. A single product spreads even a small matrix over every SM (the automatic
+// partition makes at least one band per SM); in a batch that would cut each small member into
+// many tiny bands whose set-up dominates, while the members together already fill the GPU.
+constexpr int64_t kBatchBandNnz = 160000;
+csrc_status plan_batch_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
+  if (!h->have_bt) {
+    const int64_t nnz = (int64_t)h->n + 2 * h->h;
+    const int64_t nb = std::min<int64_t>(std::max<int64_t>(1, (nnz + kBatchBandNnz - 1) / kBatchBandNnz),
+                                         std::max<int32_t>(1, h->n));
+    CSRC_TRY_S(build_plan(h, (int32_t)nb, 1, 1, h->plan_bt, h->covers_bt, nullptr));
+    h->have_bt = true;
+  }
+  *out = &h->plan_bt;
+  *covers = h->covers_bt;
+  return CSRC_OK;
+}
+
 // The plan for rk columns per pass (rk = 1, 2, 4 or 8), built on first use.
 csrc_status plan_for(csrc_matrix_s* h, int rk, DevPlan** out, bool* covers) {
   if (rk == 1) {
@@ -882,7 +905,7 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
     if (xa < ya + vb && ya < xa + vb) return fail(CSRC_ERR_ALIAS);
     DevPlan* p = nullptr;
     bool covers = false;
-    csrc_status st = plan_b1_for(h, &p, &covers);  // the batched kernel runs plain rows
+    csrc_status st = plan_batch_for(h, &p, &covers);  // plain rows, bands sized for a batch
     if (st != CSRC_OK) return fail(st);
     e->gens.push_back(h->generation);
     const bool atomic = h->tuned == CSRC_STRAT_ATOMIC || !covers;
@@ -1783,6 +1806,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   free_plan(h->plan);
   for (int i = 0; i < 3; ++i) free_plan(h->plan_rk[i]);
   free_plan(h->plan_b1);
+  free_plan(h->plan_bt);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_al_df); dfree(h->d_au_df);
   dfree(h->d_rrow); dfree(h->d_rptr); dfree(h->d_rcol); dfree(h->d_rval);
