@@ -204,10 +204,14 @@ csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy str
 /*
  * Batched products Y_b = A_b X_b (or A_b^T X_b) for b < batch, each X_b, Y_b an
  * n_b-by-nrhs row-major device block (double for CSRC_F64 storage, else float).
- * All handles must share one storage type. One persistent kernel walks a work
- * list of (matrix, band) tiles over all members. A second kernel then folds
- * every member's spilled partial sums. The pair of launches is captured in a
- * CUDA graph and replayed while the arguments stay the same.
+ * All handles must share one storage type. With nrhs = 1, one persistent kernel per
+ * lanes-per-row class walks a work list of (matrix, band) tiles over all members, largest
+ * bands first, and a second kernel folds every member's spilled partial sums; the launches
+ * are captured in a CUDA graph and replayed while the arguments stay the same. Each member
+ * runs a plan of its own for batches (bands of about 160,000 non-zeros, since the other
+ * members fill the GPU) with the window strategy, or the atomic strategy when its windows
+ * cannot hold every target. With nrhs > 1 the members run one after another through the
+ * several-right-hand-side path.
  * Asynchronous on stream.
  * Errors: INVALID_ARG, MISMATCH, ALIAS, OUT_OF_MEMORY, CUDA.
  */

@@ -177,6 +177,38 @@ def test_batched_integer_exact_and_mismatch(cs):
             cs.csrc_destroy(h)
 
 
+def test_batched_member_without_cover_runs_atomic(cs):
+    # the last row couples to one row in each of 400 window pages: no shared-memory window holds
+    # its targets, so that member's plan overflows and the batch runs it with the atomic
+    # strategy, next to members that use windows; integer values make every result exact
+    n = 64 * 400
+    ei = np.concatenate([np.arange(1, n), np.full(400, n - 1)])
+    ej = np.concatenate([np.arange(0, n - 1), np.arange(0, n - 1, 64)])  # 400 rows, one per page
+    rp, col = fe.pattern_from_edges(n, ei, ej)
+    wide = fe.FEMatrix(n, rp, col, fe.integer_values(rp, col, 11))
+    g = fe.p1_grid(20, 15, 12)
+    small = fe.FEMatrix(g.n, g.row_ptr, g.col, fe.integer_values(g.row_ptr, g.col, 13))
+    ms = [small, wide, small]
+    for storage in ("f64", "f32"):
+        hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage]) for m in ms]
+        dt = torch.float64 if storage == "f64" else torch.float32
+        try:
+            xs = [fe.integer_vector(m.n, 14 + i) for i, m in enumerate(ms)]
+            Xd = [torch.from_numpy(x).to(dt).cuda() for x in xs]
+            Yd = [torch.full_like(x, float("nan")) for x in Xd]
+            for tr in (False, True):
+                cs.csrc_spmm_batched(hs, Xd, Yd, 1, tr, torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                for m, x, y, h in zip(ms, xs, Yd, hs):
+                    c = oracle.from_matrix(m)
+                    yref = (oracle.csrc_spmv_t if tr else oracle.csrc_spmv)(c, x)
+                    np.testing.assert_array_equal(y.cpu().numpy().astype(np.float64), yref)
+                    assert cs.csrc_get_last_device_error(h) == cs.CSRC_OK
+        finally:
+            for h in hs:
+                cs.csrc_destroy(h)
+
+
 def test_autotune_spmm_k_tile(cs):
     m = fe.q1_hex(11, 1, 12)
     c = oracle.from_matrix(m)
