@@ -669,7 +669,10 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
           }
         }
       }
-      // the group's gathered sums of row r: reduced across its G lanes, added once
+      // the group's gathered sums of row r: reduced across its G lanes, added once. The
+      // double-float tree keeps each level's high-word error exactly and sums the low words
+      // without renormalising (at most four levels: the low word stays within 2^-20 of the
+      // sum); the atomic flush renormalises the high word.
 #pragma unroll
       for (int c = 0; c < RK; ++c) {
         if constexpr (MODE == MODE_DF) {
@@ -679,7 +682,7 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
             df32 u;
             u.hi = __shfl_xor_sync(gmask, t.hi, o, G);
             u.lo = __shfl_xor_sync(gmask, t.lo, o, G);
-            df_acc(t, u);
+            df_acc_short(t, u);
           }
           if (gl == 0) df_atomic_add(win.whi + rslot * RK + c, win.wlo + rslot * RK + c, t);
         } else {
