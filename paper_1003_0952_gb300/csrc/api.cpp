@@ -461,7 +461,7 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
   CSRC_TRY(upload(&p.stage_k, hp.stage_k, s));
   CSRC_TRY(upload(&p.stage_r, hp.stage_r, s));
   CSRC_TRY(cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)hp.spill * rk * h->xbytes())));
-  if (rk == 1 && B == 1) {
+  if (B == 1) {
     // window slot of every stored pair: page q of band b's window holds slots q*64 .. q*64+63.
     // Pairs whose page is outside the window (plans with overflow, which only the atomic
     // strategy runs) get slot 0.
@@ -655,9 +655,10 @@ bool is_device_ptr(const void* p) {
 BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, const void* x, void* y, void* spill,
                    int ldx, int rk, bool atomic) {
   BandArgs a;
-  // the window strategy's single-vector plain-row kernels read window slots, and with
-  // double-float arithmetic pre-split scatter operands
-  const bool local = !atomic && rk == 1 && p.block == 1;
+  // the window strategy's plain-row kernels read window slots, and with double-float
+  // arithmetic pre-split scatter operands
+  const bool local = !atomic && p.block == 1;
+  (void)rk;
   a.n = h->n;
   a.ia = h->d_ia;
   a.ja = local && p.jslot ? p.jslot : h->d_ja;

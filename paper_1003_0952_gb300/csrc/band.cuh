@@ -325,8 +325,8 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
   constexpr int XB = (int)sizeof(X);
   static_assert(!ATOMIC || RK == 1, "the atomic strategy runs single vectors");
   static_assert(B == 1 || (RK == 1 && !ATOMIC), "row blocks run single vectors with the window strategy");
-  // single vectors of plain rows with the window strategy read window slots from the ring
-  constexpr bool LOCAL = RK == 1 && B == 1 && !ATOMIC;
+  // plain rows with the window strategy (any number of columns) read window slots from the ring
+  constexpr bool LOCAL = B == 1 && !ATOMIC;
   using SV = std::conditional_t<LOCAL && MODE == MODE_DF, df32, V>;  // scatter operand as streamed
 
   extern __shared__ __align__(128) unsigned char smem[];
@@ -525,14 +525,14 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
 #pragma unroll
       for (int c = 0; c < RK; ++c) acc[c] = X(0);
       if constexpr (LOCAL) {
-        // Single vector, plain rows, window strategy: the ring carries each pair's window
-        // slot (the host wrote it in place of the column), so no page lookup is needed;
-        // slots are clamped to the window all the same. With MODE_DF the scatter operand
-        // arrives pre-split into double-float pairs. The U unrolled loads may run past the
-        // row's last pair (up to (U-1)*G pairs past the stage): they stay inside shared
-        // memory (the ring's next slot or array, or the window after the last one) and
-        // their values are never used.
-        constexpr int U = G == 16 ? 3 : 4;
+        // Plain rows, window strategy: the ring carries each pair's window slot (the host
+        // wrote it in place of the column), so no page lookup is needed; slots are clamped
+        // to the window all the same. With MODE_DF the scatter operand arrives pre-split
+        // into double-float pairs. A pair's slot and split serve all RK columns. The U
+        // unrolled loads may run past the row's last pair (up to (U-1)*G pairs past the
+        // stage): they stay inside shared memory (the ring's next slot or array, or the
+        // window after the last one) and their values are never used.
+        constexpr int U = RK == 1 ? (G == 16 ? 3 : 4) : (RK >= 4 ? 1 : 4 / RK);
         const unsigned smax = (unsigned)(nslots - 1);
         const SV* ssc = reinterpret_cast<const SV*>(ring_au + (size_t)slot * SP) - (ks & ~(kPairAlign - 1));
         const uint16_t* s16 = reinterpret_cast<const uint16_t*>(ring_ja + (size_t)slot * SP) - (ks & ~(kPairAlign - 1));
@@ -541,11 +541,11 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
           unsigned sv[U];
           V gv[U];
           SV vv[U];
-          X xv[U];
+          X xv[U][RK];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int k = k0 + u * G;
-            sv[u] = min(narrow ? (unsigned)s16[k] : (unsigned)sja[k], smax);
+            sv[u] = min(narrow ? (unsigned)s16[k] : (unsigned)sja[k], smax) * RK;
             gv[u] = sal[k];
             if constexpr (MODE == MODE_DF) {
               vv[u] = sym ? df_split<false>(gv[u], nullptr) : ssc[k];
@@ -554,19 +554,24 @@ __device__ __forceinline__ bool band_body(const BandArgs& a, const int b) {
             }
           }
 #pragma unroll
-          for (int u = 0; u < U; ++u) xv[u] = win.xs[sv[u]];
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < RK; ++c) xv[u][c] = win.xs[sv[u] + c];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             if (k0 + u * G < kx) {
-              if constexpr (MODE == MODE_DF) {
-                acc[0] = fma(gv[u], xv[u], acc[0]);
-                df_atomic_add(win.whi + sv[u], win.wlo + sv[u], df_mul(vv[u], xr[0]));
-              } else if constexpr (MODE == MODE_F64) {
-                acc[0] = fma(gv[u], xv[u], acc[0]);
-                atomicAdd(win.w + sv[u], vv[u] * xr[0]);
-              } else {
-                acc[0] = __fmaf_rn(as_f32<MODE>(gv[u]), xv[u], acc[0]);
-                atomicAdd(win.w + sv[u], __fmul_rn(as_f32<MODE>(vv[u]), xr[0]));
+#pragma unroll
+              for (int c = 0; c < RK; ++c) {
+                if constexpr (MODE == MODE_DF) {
+                  acc[c] = fma(gv[u], xv[u][c], acc[c]);
+                  df_atomic_add(win.whi + sv[u] + c, win.wlo + sv[u] + c, df_mul(vv[u], xr[c]));
+                } else if constexpr (MODE == MODE_F64) {
+                  acc[c] = fma(gv[u], xv[u][c], acc[c]);
+                  atomicAdd(win.w + sv[u] + c, vv[u] * xr[c]);
+                } else {
+                  acc[c] = __fmaf_rn(as_f32<MODE>(gv[u]), xv[u][c], acc[c]);
+                  atomicAdd(win.w + sv[u] + c, __fmul_rn(as_f32<MODE>(vv[u]), xr[c]));
+                }
               }
             }
           }

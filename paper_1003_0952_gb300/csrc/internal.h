@@ -143,8 +143,8 @@ struct DevPlan {
   int32_t smem_bytes = 0;      // dynamic shared memory of a band CTA (ring + window + table)
   std::vector<int64_t> band_pairs;  // host copy: stored pairs of each band (batched scheduling)
   int64_t total_pages = 0;
-  // single-vector plans of plain rows: the window slot of every stored pair, written in
-  // place of its column for the window strategy (h entries, padded like ja)
+  // plans of plain rows: the window slot of every stored pair, written in place of its
+  // column for the window strategy (h entries, padded like ja)
   int32_t* jslot = nullptr;
   uint16_t* jslot16 = nullptr;   // the same slots as 16 bits (index compression); jslot is then null
 };
@@ -154,7 +154,7 @@ struct BandArgs {
   int32_t n;
   const int32_t* ia;
   const int32_t* ja;  // columns; window slots (DevPlan::jslot) for the window strategy's
-                      // single-vector plain-row kernels
+                      // plain-row kernels
   const uint16_t* ja16;  // 16-bit window slots in place of ja for those kernels (index
                          // compression), else null
   const int32_t* band_stage;
