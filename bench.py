@@ -154,6 +154,12 @@ def reduce_max(v: float, world: int, device) -> float:
     return float(t.item())
 
 
+def replica_throughput(world: int, bytes_per_step: float, steps: int, seconds: float) -> float:
+    """Whole-job GB/s of `world` replicas that each moved bytes_per_step per step for `steps`
+    steps, timed by the slowest rank (seconds = max over ranks)."""
+    return world * bytes_per_step * steps / seconds / 1e9
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -332,8 +338,8 @@ def run_ours(args):
         cs.csrc_destroy(h)
 
     nbytes_step = 2 * int(info["model_bytes"])
-    value = world * nbytes_step * args.steps / (ms * 1e-3) / 1e9
-    e2e_value = world * nbytes_step * args.steps / e2e_s / 1e9
+    value = replica_throughput(world, nbytes_step, args.steps, ms * 1e-3)
+    e2e_value = replica_throughput(world, nbytes_step, args.steps, e2e_s)
     peak, peak_src = measured_hbm()
     nprod, ms_prod = ktimes["product"]
     # algorithmic bytes of one band-kernel launch: the CSRC working set plus its spill writes
