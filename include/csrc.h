@@ -323,6 +323,17 @@ csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out);
 csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_t maxit, csrc_strategy strategy,
                       int32_t* iters_out, double* relres_out, cudaStream_t stream);
 
+/*
+ * Self-test of the kernels' bounded waits (failure detection without a GPU fault): one CTA
+ * waits, with the same bounded mbarrier wait the band kernels use, on a barrier that
+ * nothing arrives at, giving up after `cycles` SM clock cycles (clamped to [1000, 2e9]).
+ * The expected result is CSRC_ERR_DEVICE_TIMEOUT, read back from a device status word
+ * after the kernel has returned normally; the CUDA context stays usable. Returns CSRC_OK
+ * only if the wait completed (it cannot), CSRC_ERR_CUDA on a runtime error.
+ * Synchronous (default stream of the current device).
+ */
+csrc_status csrc_selftest_bounded_wait(int64_t cycles);
+
 /* Fill *info (host). */
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info);
 

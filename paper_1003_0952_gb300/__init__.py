@@ -91,6 +91,7 @@ SIGNATURES = {
     "csrc_create_rect_from_csr": (ctypes.c_int, [_P(_VP), ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP, ctypes.c_int,
                                                  ctypes.c_uint32, _VP]),
     "csrc_partition": (ctypes.c_int, [_VP, ctypes.c_int32, _VP]),
+    "csrc_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64]),
     "csrc_bicg": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, _P(ctypes.c_int32),
                                  _P(ctypes.c_double), _VP]),
     "csrc_color": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(ctypes.c_int32), _VP]),
@@ -248,6 +249,11 @@ def csrc_bicg(h, b, x, rtol=1e-10, maxit=1000, strategy=CSRC_STRAT_AUTO, stream=
     if st not in (CSRC_OK, CSRC_ERR_NOT_CONVERGED, CSRC_ERR_BREAKDOWN):
         _check(st, "csrc_bicg")
     return {"status": st, "iters": it.value, "relres": rr.value}
+
+
+def csrc_selftest_bounded_wait(cycles=2_000_000) -> int:
+    """Run the bounded-wait self-test; returns the status (CSRC_ERR_DEVICE_TIMEOUT expected)."""
+    return _lib.csrc_selftest_bounded_wait(int(cycles))
 
 
 def csrc_autotune(h, x, y, stream=None) -> None:

@@ -1757,6 +1757,20 @@ csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_
   return finish(maxit, CSRC_ERR_NOT_CONVERGED);
 }
 
+csrc_status csrc_selftest_bounded_wait(int64_t cycles) {
+  const long long limit = (long long)std::min<int64_t>(std::max<int64_t>(cycles, 1000), 2000000000LL);
+  int32_t* status = nullptr;
+  CSRC_TRY(dmalloc(&status, 1));
+  int32_t w = 0;
+  cudaError_t e = cudaMemset(status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = launch_wait_probe(limit, status, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&w, status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(status);
+  CSRC_TRY(e);
+  return (w & DEV_TIMEOUT) ? CSRC_ERR_DEVICE_TIMEOUT : CSRC_OK;
+}
+
 csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   if (!h || !info) return CSRC_ERR_INVALID_ARG;
   std::memset(info, 0, sizeof(*info));

@@ -82,13 +82,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return done != 0u;
 }
 
-// Bounded wait for the phase with the given parity: gives up after about two
-// seconds (clock64 at ~2 GHz) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity: gives up after `limit` SM clock
+// cycles (by default about two seconds at ~2 GHz) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = 4000000000LL) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > 4000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }

@@ -221,6 +221,9 @@ int solver_blocks(int sms);
 cudaError_t launch_solver_op(int op, bool fp64, int64_t n, int nblocks, double scalar, const void* v0, const void* v1,
                              const void* v2, void* w0, void* w1, void* w2, void* w3, double* partial, double* out,
                              cudaStream_t s);
+// Bounded-wait self-test (kernels.cu): one CTA waits `limit` cycles on an mbarrier that
+// nothing arrives at and ORs DEV_TIMEOUT into *status.
+cudaError_t launch_wait_probe(long long limit, int32_t* status, cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_rk();
 cudaError_t prepare_band_kernels_block();

@@ -22,6 +22,28 @@ __global__ void accumulate_kernel(int64_t nacc, int rk, int ldx, const int32_t* 
   y[(size_t)row * ldx + c] = s;
 }
 
+// ---------------------------------------------------------------------------- bounded-wait self-test
+// One CTA waits, with the band kernels' bounded wait, on an mbarrier that nothing arrives at:
+// the wait must give up after `limit` cycles and record DEV_TIMEOUT in *status.
+__global__ void wait_probe_kernel(long long limit, int32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1u);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(b, 0u, limit)) atomicOr(status, DEV_TIMEOUT);
+    mbar_inval(b);
+  }
+}
+
+cudaError_t launch_wait_probe(long long limit, int32_t* status, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(limit, status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- double-float split
 __global__ void split_df_kernel(const double* __restrict__ v, df32* __restrict__ out, int64_t count) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)

@@ -348,6 +348,24 @@ def test_index_compression(cs, storage):
                 hh.close()
 
 
+# --------------------------------------------------------------------------- failure detection
+def test_bounded_wait_gives_up_and_the_context_stays_usable(cs):
+    # a barrier nothing arrives at: the bounded wait gives up after ~1 ms, the kernel returns
+    # normally and the host reads DEVICE_TIMEOUT from the status word
+    import time
+
+    t0 = time.perf_counter()
+    assert cs.csrc_selftest_bounded_wait(2_000_000) == cs.CSRC_ERR_DEVICE_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    m = fe.q1_hex(6, 1, 131)
+    x = fe.source_vector(m.n, 132)
+    h = Handle(cs, m)
+    try:
+        _check(m, x, h.run(x), False, TOL["f64"])
+    finally:
+        h.close()
+
+
 # --------------------------------------------------------------------------- interface behaviour
 def test_host_pointers_are_staged(cs):
     m = fe.p1_grid(50, 40, 9)
