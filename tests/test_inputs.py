@@ -33,3 +33,24 @@ def test_batch_sizes_are_log_uniform_in_range():
     ns = np.array([m.n for m in ms])
     assert ns.min() >= 1000 and ns.max() <= 500_000
     assert {m.meta["kind"] for m in ms} <= {"p1", "kuhn"}
+
+
+def test_overlap_subdomain_layout():
+    # one subdomain of an overlapping decomposition: own unknowns first, then the overlap in
+    # increasing global order; columns stay sorted and the square block is the leading block
+    g = fe.q1_hex(6, 3, 41)
+    for n_sub in (1, g.n // 3, g.n // 2, g.n):
+        a = fe.overlap_subdomain(g, n_sub)
+        assert a.n == n_sub and a.m >= a.n
+        assert a.row_ptr[0] == 0 and a.row_ptr[-1] == a.nnz == int(g.row_ptr[n_sub])
+        for i in range(a.n):
+            c = a.col[a.row_ptr[i]:a.row_ptr[i + 1]]
+            assert np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < a.m
+            gc = g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
+            np.testing.assert_array_equal(c[c < a.n], gc[gc < a.n])
+        ext = a.meta["overlap"]
+        assert len(ext) == a.m - a.n and np.all(np.diff(ext) > 0) and (len(ext) == 0 or ext.min() >= n_sub)
+        # every overlap column is reached by some row
+        assert np.all(np.bincount(a.col, minlength=a.m)[a.n:] > 0)
+    assert fe.overlap_subdomain(g, g.n).m == g.n
+
