@@ -71,16 +71,28 @@ typedef enum { CSRC_F64 = 0, CSRC_F32 = 1, CSRC_BF16 = 2 } csrc_dtype; /* storag
 
 typedef enum {
   CSRC_STRAT_AUTO = 0,   /* the handle's tuned choice (CSRC_STRAT_WINDOW until csrc_autotune() runs) */
-  CSRC_STRAT_WINDOW = 1, /* private shared-memory windows + deterministic accumulation kernel */
+  CSRC_STRAT_WINDOW = 1, /* private windows (Section 3.1 local buffers) whose scatter is sorted by target
+                            when the plan is built: every window row is summed by one lane, with no
+                            atomics; rows below a band are folded in by a deterministic accumulation
+                            kernel. Bitwise reproducible from run to run. */
   CSRC_STRAT_COLOR = 2,  /* colour-ordered rows, no atomics (needs csrc_color()) */
-  CSRC_STRAT_ATOMIC = 3  /* shared-memory windows flushed with global FP64/FP32 atomic adds */
+  CSRC_STRAT_ATOMIC = 3, /* stream-order windows flushed with global FP64/FP32 atomic adds */
+  CSRC_STRAT_WINDOW_ATOMIC = 4 /* stream-order windows: each pair scatters into the shared-memory window
+                                  with an atomic add as it streams past, rows below a band go through the
+                                  accumulation kernel (the same deterministic fold as CSRC_STRAT_WINDOW) */
 } csrc_strategy;
 
 enum {
   CSRC_FLAG_PAD_PATTERN = 1, /* add an explicit zero a_ji for every a_ij without a mirror */
   CSRC_FLAG_ONE_BASED = 2,   /* row_ptr / row / col are 1-based (Fortran, as in Fig. 2) */
-  CSRC_FLAG_FP64_ARITH = 4,  /* CSRC_F64 only: multiply and add on the FP64 pipe (bit-for-bit IEEE
-                                double products) instead of the default double-float arithmetic */
+  CSRC_FLAG_FP64_ARITH = 4,  /* CSRC_F64 only: every multiply and add on the FP64 pipe. This is the
+                                default for CSRC_F64 storage; the flag is accepted for clarity */
+  CSRC_FLAG_DF32_ARITH = 64, /* CSRC_F64 only, stream-order strategies (CSRC_STRAT_WINDOW_ATOMIC and
+                                CSRC_STRAT_ATOMIC): the scatter products and window sums in double-float
+                                arithmetic on the FP32 pipes (about 2^-46 relative per operation instead of
+                                2^-53, values and x within [2^-50, 2^63) in magnitude), the gather on the
+                                FP64 pipe. CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR and products with several
+                                right-hand sides keep FP64 arithmetic */
   CSRC_FLAG_SYMMETRIC_VALUES = 16, /* numerically symmetric matrix (Section 2.2): every a_ji equals a_ij
                                      bit for bit (checked at creation), au is not stored and the
                                      kernels scatter with al, so a product streams 12 instead of 20
@@ -102,8 +114,9 @@ typedef struct {
   int32_t storage;          /* csrc_dtype */
   int32_t arith;            /* 0 = double-float, 1 = FP64 pipe, 2 = FP32 */
   int64_t model_bytes;      /* ia + ja + al + au + ad + x + y (Table 1's ws for CSRC_F64) */
-  int32_t nbands;           /* execution bands of the window plan (0 before it is built) */
-  int32_t page_rows;        /* rows per window page */
+  int32_t nbands;           /* execution bands of the window plan (0 before it is built); the window
+                               strategy's lists when built, else the stream-order plan's */
+  int32_t page_rows;        /* rows per window page of the stream-order plan (0 for the lists) */
   int64_t spill_entries;    /* window slots written to the spill buffer per product */
   int64_t spill_rows;       /* rows that receive spilled partial sums */
   int64_t accum_bytes;      /* accumulation traffic per product (spill write+read, indices, y update) */
@@ -117,6 +130,14 @@ typedef struct {
   int32_t block;            /* rows per node block the single-vector product runs (1 = plain rows) */
   int64_t m;                /* columns: n for square handles, m >= n for rectangular ones */
   int64_t rect_nnz;         /* entries of the auxiliary CSR of a rectangular handle (0 when square) */
+  /* the window strategy's lists (0 before they are built): */
+  int64_t list_entries;     /* list entries of all bands (n + 2h) */
+  int64_t list_slices;      /* slices of 32 window rows */
+  int64_t list_lane_steps;  /* lanes issued: 32 x the longest list of every slice (>= list_entries) */
+  int64_t list_bytes;       /* bytes the window strategy's product kernel moves per product */
+  /* the stream-order plan (window-atomic and atomic strategies; 0 before it is built): */
+  int32_t stream_nbands;
+  int64_t stream_spill_entries;
 } csrc_info;
 
 /*
@@ -230,7 +251,7 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
  * creates its handle and calls csrc_partition once at set-up, then uses this call.
  *
  * It computes what csrc_spmv / csrc_spmv_t compute with CSRC_STRAT_WINDOW, with the
- * same kernels. The only difference is that the spilled partial sums go to a fixed
+ * same kernels (bit for bit: the window strategy sums every row in a fixed order). The only difference is that the spilled partial sums go to a fixed
  * array of CSRC_NOALLOC_MAX_SPILL_ENTRIES values that the library holds in static
  * device memory (16 MiB on every GPU that loads the library, kept until the process
  * exits), instead of the buffer the handle allocates.
@@ -241,7 +262,8 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
  *   stream     asynchronous on this stream
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current. Make that first call before any
- * stream capture.
+ * stream capture. The call makes the handle's device current while it runs and gives
+ * the caller's current device back before it returns.
  * Sharing: every call on a device, from any handle, uses the same array, which keeps
  * the last call's contents. The band kernel writes every slot the accumulation reads,
  * so nothing needs clearing between calls, but calls that overlap on the GPU (other

@@ -40,14 +40,15 @@ CSRC_ERR_BREAKDOWN = 16
 # storage (csrc_dtype)
 CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
 # strategies (csrc_strategy)
-CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC = 0, 1, 2, 3
+CSRC_STRAT_AUTO, CSRC_STRAT_WINDOW, CSRC_STRAT_COLOR, CSRC_STRAT_ATOMIC, CSRC_STRAT_WINDOW_ATOMIC = 0, 1, 2, 3, 4
 # flags
 CSRC_FLAG_PAD_PATTERN, CSRC_FLAG_ONE_BASED, CSRC_FLAG_FP64_ARITH, CSRC_FLAG_NODE_BLOCKS = 1, 2, 4, 8
 CSRC_FLAG_SYMMETRIC_VALUES = 16
 CSRC_FLAG_COMPRESS_INDICES = 32
+CSRC_FLAG_DF32_ARITH = 64
 
 STRATEGIES = {"auto": CSRC_STRAT_AUTO, "window": CSRC_STRAT_WINDOW, "color": CSRC_STRAT_COLOR,
-              "atomic": CSRC_STRAT_ATOMIC}
+              "atomic": CSRC_STRAT_ATOMIC, "window_atomic": CSRC_STRAT_WINDOW_ATOMIC}
 STORAGE = {"f64": CSRC_F64, "f32": CSRC_F32, "bf16": CSRC_BF16}
 
 
@@ -66,6 +67,8 @@ class csrc_info(ctypes.Structure):
         ("smem_bytes", ctypes.c_int32), ("ncolors", ctypes.c_int32), ("tuned_strategy", ctypes.c_int32),
         ("tuned_rk", ctypes.c_int32), ("group", ctypes.c_int32), ("nstages", ctypes.c_int64),
         ("block", ctypes.c_int32), ("m", ctypes.c_int64), ("rect_nnz", ctypes.c_int64),
+        ("list_entries", ctypes.c_int64), ("list_slices", ctypes.c_int64), ("list_lane_steps", ctypes.c_int64),
+        ("list_bytes", ctypes.c_int64), ("stream_nbands", ctypes.c_int32), ("stream_spill_entries", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -55,17 +55,23 @@ struct csrc_matrix_s {
   int32_t* d_trow = nullptr;
   void* d_tval = nullptr;
   bool rect() const { return m != n; }
-  // partition (Section 3.1 rule) and the window plan built from it
+  // partition (Section 3.1 rule) and the plans built from it
   std::vector<int32_t> part;
+  // owner lists of the window strategy: single vectors, and rk = 2, 4, 8 columns per pass
+  OwnerPlan oplan;
+  bool have_oplan = false;
+  OwnerPlan oplan_rk[3];
+  bool have_orp[3] = {false, false, false};
+  bool fits_orp[3] = {false, false, false};
+  // owner lists sized for batches (bands of about kBatchBandNnz non-zeros)
+  OwnerPlan oplan_bt;
+  bool have_obt = false;
+  // stream-order plan of the window-atomic and atomic strategies
   DevPlan plan;
   bool have_plan = false;
   bool plan_covers = false;   // every scatter target lies in its band's window
   int32_t part_nbands = 0;    // band count requested for the partition (0 = automatic)
-  // plans for several right-hand sides: RK = 2, 4, 8 columns per pass (windows RK times wider)
-  DevPlan plan_rk[3];
-  bool have_rk[3] = {false, false, false};
-  bool covers_rk[3] = {false, false, false};
-  bool fits_rk[3] = {false, false, false};
+  int32_t owner_nbands = 0;   // band count of the owner plans (0 = automatic; set by the autotuner)
   int32_t block = 1;          // rows per node block found at creation (1 = none)
   DevPlan plan_b1;            // plain-row plan when the main plan uses node blocks
   bool have_b1 = false;
@@ -512,33 +518,88 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
   return CSRC_OK;
 }
 
-// The single-vector plan (and the partition it comes from); plans for several
-// right-hand sides are rebuilt from the same band count when next needed.
-csrc_status make_plan(csrc_matrix_s* h, int32_t nbands) {
+// ---------------------------------------------------------------------------- owner plans
+// Automatic band count of an owner plan: a multiple of the CTAs the GPU holds at once
+// (SMs x resident CTAs for rk columns), with about kOwnerBandNnz non-zeros per band, so
+// that the bands of equal weight finish in whole waves.
+constexpr int64_t kOwnerBandNnz = 80000;
+int32_t owner_auto_bands(const csrc_matrix_s* h, int rk) {
+  const int64_t nnz = (int64_t)h->n + 2 * h->h;
+  const int64_t slots = (int64_t)h->sms * owner_ctas_per_sm(rk);
+  int64_t waves = (nnz + slots * kOwnerBandNnz - 1) / (slots * kOwnerBandNnz);
+  if (waves < 1) waves = 1;
+  return (int32_t)std::min<int64_t>(slots * waves, std::max<int32_t>(1, h->n));
+}
+
+// Owner lists for rk columns per pass from the Section 3.1 partition into nbands bands
+// (0 = automatic); bands whose windows exceed shared memory are split further.
+csrc_status build_owner(csrc_matrix_s* h, int rk, int32_t nbands, OwnerPlan& p, std::vector<int32_t>* part_out) {
+  const int32_t nb = nbands > 0 ? std::min<int32_t>(nbands, std::max<int32_t>(1, h->n)) : owner_auto_bands(h, rk);
+  std::vector<int32_t> part;
+  nnz_partition(h->ia, 0, h->n, nb, part);
+  const int ab = (int)h->xbytes();  // window x and accumulation: double for FP64 storage, else float
+  CSRC_TRY_S(build_owner_plan(h->n, h->h, h->ia, h->ja, part, rk, ab, owner_smem_budget(rk), (int)h->vbytes(), ab,
+                              h->d_al, h->au_ptr(), h->d_ad, h->sym, p));
+  if (part_out) part_out->swap(part);
+  return CSRC_OK;
+}
+
+void drop_owner_plans(csrc_matrix_s* h) {
+  free_owner_plan(h->oplan);
+  h->have_oplan = false;
   for (int i = 0; i < 3; ++i) {
-    free_plan(h->plan_rk[i]);
-    h->have_rk[i] = false;
+    free_owner_plan(h->oplan_rk[i]);
+    h->have_orp[i] = h->fits_orp[i] = false;
   }
+}
+
+// The owner plan for rk = 1, 2, 4 or 8 columns per pass, built on first use. Single vectors
+// use the band count of csrc_partition (or the autotuner's); wider passes pick their own.
+csrc_status owner_for(csrc_matrix_s* h, int rk, OwnerPlan** out) {
+  if (rk == 1) {
+    if (!h->have_oplan) {
+      CSRC_TRY_S(build_owner(h, 1, h->owner_nbands, h->oplan, &h->part));
+      h->have_oplan = true;
+      ++h->generation;
+    }
+    *out = &h->oplan;
+    return CSRC_OK;
+  }
+  const int i = rk == 2 ? 0 : (rk == 4 ? 1 : 2);
+  if (!h->have_orp[i]) {
+    const csrc_status st = build_owner(h, rk, 0, h->oplan_rk[i], nullptr);
+    if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
+    h->have_orp[i] = true;  // remembered either way: a window of rk columns may not fit
+    h->fits_orp[i] = st == CSRC_OK;
+  }
+  if (!h->fits_orp[i]) return CSRC_ERR_NOT_PARTITIONED;
+  *out = &h->oplan_rk[i];
+  return CSRC_OK;
+}
+
+// ---------------------------------------------------------------------------- stream-order plans
+// The stream-order plan of the window-atomic and atomic strategies, from the band count of
+// csrc_partition (0 = automatic); built on first use.
+csrc_status make_plan(csrc_matrix_s* h) {
   h->have_plan = false;
   free_plan(h->plan_b1);
   h->have_b1 = false;
   csrc_status st = CSRC_ERR_NOT_PARTITIONED;
   if (h->block > 1) {
-    st = build_plan(h, nbands, 1, h->block, h->plan, h->plan_covers, &h->part);
+    st = build_plan(h, h->part_nbands, 1, h->block, h->plan, h->plan_covers, nullptr);
     if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
     if (st == CSRC_OK && !h->plan_covers) st = CSRC_ERR_NOT_PARTITIONED;
   }
-  if (st != CSRC_OK) CSRC_TRY_S(build_plan(h, nbands, 1, 1, h->plan, h->plan_covers, &h->part));
-  h->part_nbands = nbands;
+  if (st != CSRC_OK) CSRC_TRY_S(build_plan(h, h->part_nbands, 1, 1, h->plan, h->plan_covers, nullptr));
   h->have_plan = true;
   ++h->generation;
   return CSRC_OK;
 }
 
-// A single-vector plan of plain rows (the atomic strategy and the batched kernel run
-// rows one at a time): the main plan, or, when that one uses node blocks, a second plan.
+// A single-vector stream-order plan of plain rows (the atomic strategy and the batched kernel
+// run rows one at a time): the main plan, or, when that one uses node blocks, a second plan.
 csrc_status plan_b1_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
-  if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
+  if (!h->have_plan) CSRC_TRY_S(make_plan(h));
   if (h->plan.block == 1) {
     *out = &h->plan;
     *covers = h->plan_covers;
@@ -568,32 +629,6 @@ csrc_status plan_batch_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
   }
   *out = &h->plan_bt;
   *covers = h->covers_bt;
-  return CSRC_OK;
-}
-
-// The plan for rk columns per pass (rk = 1, 2, 4 or 8), built on first use.
-csrc_status plan_for(csrc_matrix_s* h, int rk, DevPlan** out, bool* covers) {
-  if (rk == 1) {
-    if (!h->have_plan) CSRC_TRY_S(make_plan(h, 0));
-    *out = &h->plan;
-    *covers = h->plan_covers;
-    return CSRC_OK;
-  }
-  const int i = rk == 2 ? 0 : (rk == 4 ? 1 : 2);
-  if (!h->have_rk[i]) {
-    const csrc_status st = build_plan(h, h->part_nbands, rk, 1, h->plan_rk[i], h->covers_rk[i], nullptr);
-    if (st == CSRC_ERR_NOT_PARTITIONED) {
-      h->have_rk[i] = true;  // remembered: no window of rk columns fits this matrix
-      h->fits_rk[i] = false;
-      return st;
-    }
-    CSRC_TRY_S(st);
-    h->have_rk[i] = true;
-    h->fits_rk[i] = true;
-  }
-  if (!h->fits_rk[i]) return CSRC_ERR_NOT_PARTITIONED;
-  *out = &h->plan_rk[i];
-  *covers = h->covers_rk[i];
   return CSRC_OK;
 }
 
@@ -633,12 +668,24 @@ void release_timing(csrc_matrix_s* h) {
   h->timed.clear();
 }
 
-csrc_status ensure_device(csrc_matrix_s* h) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return CSRC_ERR_CUDA;
-  if (dev != h->device) CSRC_TRY(cudaSetDevice(h->device));
-  return CSRC_OK;
-}
+// Makes the handle's device current for the duration of an entry point and gives the
+// caller's current device back when the entry point returns (nested entries that find the
+// handle's device already current change nothing).
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  csrc_status enter(const csrc_matrix_s* h) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return CSRC_ERR_CUDA;
+    if (prev != h->device) {
+      if (cudaSetDevice(h->device) != cudaSuccess) return CSRC_ERR_CUDA;
+      switched = true;
+    }
+    return CSRC_OK;
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
@@ -690,9 +737,41 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
   return a;
 }
 
+// Arguments of one owner-kernel launch on plan p: A x, or A^T x with the exchanged values
+// (Section 5); x and y point at the pass's first column, ldx is their row stride.
+OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y, void* spill, int ldx) {
+  OwnerArgs a;
+  a.band = p.band;
+  a.band_slice = p.band_slice;
+  a.slice_off = p.slice_off;
+  a.lane = p.lane;
+  a.spill_row = p.spill_row;
+  a.S = p.S;
+  a.V = transpose ? p.VT : p.VA;
+  a.x = x;
+  a.y = y;
+  a.spill = spill;
+  a.ldx = ldx;
+  a.band_offset = 0;
+  return a;
+}
+
+// The window strategy on owner plan p: the owner kernel, then the accumulation of spills.
+csrc_status run_owner(csrc_matrix_s* h, const OwnerPlan& p, bool transpose, const void* x, void* y, void* spill,
+                      int ldx, int rk, cudaStream_t s) {
+  const OwnerArgs a = owner_args(p, transpose, x, y, spill, ldx);
+  CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
+                        [&] { return launch_owner(h->storage, rk, a, p.nb, p.smem_bytes, s); }));
+  if (p.nacc > 0)
+    CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
+      return launch_accumulate(h->arith, h->storage, p.nacc, rk, ldx, p.acc_row, p.acc_ptr, p.acc_src, spill, y, s);
+    }));
+  return CSRC_OK;
+}
+
 csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st, cudaStream_t s, bool transpose) {
   if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
-  if (st < CSRC_STRAT_AUTO || st > CSRC_STRAT_ATOMIC) return CSRC_ERR_INVALID_ARG;
+  if (st < CSRC_STRAT_AUTO || st > CSRC_STRAT_WINDOW_ATOMIC) return CSRC_ERR_INVALID_ARG;
   if (h->m == 0) return CSRC_OK;
   // x and y lengths: n each, or m and n (A x) / n and m (A^T x) for a rectangular matrix
   const size_t vb = (size_t)h->n * h->xbytes();
@@ -701,18 +780,19 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
   if (xa < ya + yb && ya < xa + xb) return CSRC_ERR_ALIAS;
-  CSRC_TRY_S(ensure_device(h));
-  if (h->n == 0) {  // no square part: only A_R^T x can be non-zero
-    if (!transpose) return CSRC_OK;
-  } else if (!h->have_plan) {
-    CSRC_TRY_S(make_plan(h, 0));
-  }
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   csrc_strategy strat = st;
   if (strat == CSRC_STRAT_AUTO) strat = h->tuned ? (csrc_strategy)h->tuned : CSRC_STRAT_WINDOW;
-  if (h->n > 0 && strat == CSRC_STRAT_WINDOW && !h->plan_covers) {
-    if (st == CSRC_STRAT_AUTO) strat = CSRC_STRAT_ATOMIC;
-    else return CSRC_ERR_NOT_PARTITIONED;
+  OwnerPlan* op = nullptr;
+  if (h->n > 0 && strat == CSRC_STRAT_WINDOW) {
+    const csrc_status ps = owner_for(h, 1, &op);
+    if (ps == CSRC_ERR_NOT_PARTITIONED && st == CSRC_STRAT_AUTO) strat = CSRC_STRAT_ATOMIC;  // no window fits
+    else if (ps != CSRC_OK) return ps;
   }
+  if (h->n > 0 && (strat == CSRC_STRAT_WINDOW_ATOMIC || strat == CSRC_STRAT_ATOMIC) && !h->have_plan)
+    CSRC_TRY_S(make_plan(h));
+  if (h->n > 0 && strat == CSRC_STRAT_WINDOW_ATOMIC && !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
   if (h->n > 0 && strat == CSRC_STRAT_COLOR && h->ncolors == 0) return CSRC_ERR_NOT_COLORED;
   // host vectors are staged through handle-owned device buffers (m entries: room for either)
   const size_t sb = (size_t)h->m * h->xbytes();
@@ -732,6 +812,8 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
   const void* sc = transpose ? h->d_al : h->au_ptr(); // scattered values
   if (h->n == 0) {
     // nothing to do for A_S
+  } else if (strat == CSRC_STRAT_WINDOW) {
+    CSRC_TRY_S(run_owner(h, *op, transpose, dx, dy, op->spill_buf, 1, 1, s));
   } else if (strat == CSRC_STRAT_COLOR) {
     CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
     for (int32_t c = 0; c < h->ncolors; ++c) {
@@ -768,14 +850,14 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
       }));
     }
   }
-  (void)vb;
   if (!ydev) CSRC_TRY(cudaMemcpyAsync(y, dy, yb, cudaMemcpyDeviceToHost, s));
   return CSRC_OK;
 }
 
 // Y = A X (or A^T X) for one handle, X and Y n-by-nrhs row-major device blocks: the
 // columns are cut into passes of rk = 8, 4, 2 or 1 columns (the handle's tuned k-tile caps
-// rk), and each pass runs the band kernel and the accumulation kernel on its columns.
+// rk; a pass falls back to fewer columns when no window of rk columns fits), and each pass
+// runs the owner kernel and the accumulation kernel on its columns.
 csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, bool transpose, cudaStream_t s) {
   if (h->n == 0) return CSRC_OK;
   const size_t vb = (size_t)h->n * (size_t)nrhs * h->xbytes();
@@ -783,35 +865,22 @@ csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, boo
   const char* ya = static_cast<const char*>(Y);
   if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
   if (!is_device_ptr(X) || !is_device_ptr(Y)) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   const int cap = h->tuned_rk > 0 ? h->tuned_rk : 8;
   for (int32_t c0 = 0; c0 < nrhs;) {
     int rk = 8;
     while (rk > 1 && (rk > cap || c0 + rk > nrhs)) rk /= 2;
-    // a wider pass needs a wider window: when no band of rk columns fits in shared
-    // memory, fall back to fewer columns per pass
-    DevPlan* p = nullptr;
-    bool covers = false;
+    OwnerPlan* p = nullptr;
     while (true) {
-      const csrc_status st = plan_for(h, rk, &p, &covers);
-      if (st == CSRC_OK && (covers || rk == 1)) break;
-      if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
-      if (rk == 1) return st;
+      const csrc_status st = owner_for(h, rk, &p);
+      if (st == CSRC_OK) break;
+      if (st != CSRC_ERR_NOT_PARTITIONED || rk == 1) return st;
       rk /= 2;
     }
     const void* xc = static_cast<const char*>(X) + (size_t)c0 * h->xbytes();
     void* yc = static_cast<char*>(Y) + (size_t)c0 * h->xbytes();
-    const bool atomic = !covers;  // single column whose plan overflows: atomic strategy
-    if (atomic)
-      CSRC_TRY(cudaMemset2DAsync(yc, (size_t)nrhs * h->xbytes(), 0, h->xbytes(), (size_t)h->n, s));
-    const BandArgs a = band_args(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk, atomic);
-    CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
-                          [&] { return launch_band(h->arith, h->storage, atomic, a, p->nb, p->smem_bytes, s); }));
-    if (!atomic && p->nacc > 0)
-      CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
-        return launch_accumulate(h->arith, h->storage, p->nacc, rk, nrhs, p->acc_row, p->acc_ptr, p->acc_src,
-                                 p->spill_buf, yc, s);
-      }));
+    CSRC_TRY_S(run_owner(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk, s));
     c0 += rk;
   }
   return CSRC_OK;
@@ -1133,7 +1202,8 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   if (m->sms <= 0) m->sms = 1;
   if (storage == CSRC_F64) {
-    m->arith = (flags & CSRC_FLAG_FP64_ARITH) ? ARITH_F64 : ARITH_DF32;
+    // FP64 arithmetic unless double-float is asked for (stream-order strategies only)
+    m->arith = ((flags & CSRC_FLAG_DF32_ARITH) && !(flags & CSRC_FLAG_FP64_ARITH)) ? ARITH_DF32 : ARITH_F64;
     // the double-float path needs values in [2^-50, 2^63) (or zero); otherwise use FP64 arithmetic
     auto in_range = [](double v) {
       if (v == 0.0) return true;
@@ -1211,7 +1281,8 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   {
     std::lock_guard<std::mutex> lk(g_setup_mutex);
     if (!g_prepared) {
-      if (prepare_band_kernels() != cudaSuccess || prepare_batch_kernels() != cudaSuccess) {
+      if (prepare_band_kernels() != cudaSuccess || prepare_batch_kernels() != cudaSuccess ||
+          prepare_owner_kernels() != cudaSuccess) {
         cudaGetLastError();
         return fail(CSRC_ERR_CUDA);
       }
@@ -1240,14 +1311,14 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   const char* xa = static_cast<const char*>(x);
   const char* ya = static_cast<const char*>(y);
   if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
-  if (!h->have_plan || !h->plan_covers) return CSRC_ERR_NOT_PARTITIONED;
-  if (h->plan.spill > capacity) return CSRC_ERR_INVALID_ARG;
+  if (!h->have_oplan) return CSRC_ERR_NOT_PARTITIONED;
+  if (h->oplan.spill > capacity) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
-  const BandArgs a = band_args(h, h->plan, transpose, x, y, spill, 1, 1, false);
-  CSRC_TRY(launch_band(h->arith, h->storage, false, a, h->plan.nb, h->plan.smem_bytes, s));
-  if (h->plan.nacc > 0)
-    CSRC_TRY(launch_accumulate(h->arith, h->storage, h->plan.nacc, 1, 1, h->plan.acc_row, h->plan.acc_ptr,
-                               h->plan.acc_src, spill, y, s));
+  const OwnerPlan& p = h->oplan;
+  const OwnerArgs a = owner_args(p, transpose, x, y, spill, 1);
+  CSRC_TRY(launch_owner(h->storage, 1, a, p.nb, p.smem_bytes, s));
+  if (p.nacc > 0)
+    CSRC_TRY(launch_accumulate(h->arith, h->storage, p.nacc, 1, 1, p.acc_row, p.acc_ptr, p.acc_src, spill, y, s));
   return CSRC_OK;
 }
 
@@ -1263,7 +1334,7 @@ csrc_status csrc_create_from_csr(csrc_handle* out, int32_t n, const int64_t* row
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
                          CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES |
-                         CSRC_FLAG_COMPRESS_INDICES))
+                         CSRC_FLAG_COMPRESS_INDICES | CSRC_FLAG_DF32_ARITH))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1294,7 +1365,7 @@ csrc_status csrc_create_rect_from_csr(csrc_handle* out, int32_t n, int32_t m, co
   if (storage < CSRC_F64 || storage > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
   if (flags & ~(uint32_t)(CSRC_FLAG_PAD_PATTERN | CSRC_FLAG_ONE_BASED | CSRC_FLAG_FP64_ARITH |
                          CSRC_FLAG_NODE_BLOCKS | CSRC_FLAG_SYMMETRIC_VALUES |
-                         CSRC_FLAG_COMPRESS_INDICES))
+                         CSRC_FLAG_COMPRESS_INDICES | CSRC_FLAG_DF32_ARITH))
     return CSRC_ERR_INVALID_ARG;
   const int64_t base = (flags & CSRC_FLAG_ONE_BASED) ? 1 : 0;
   if (row_ptr[0] != base) return CSRC_ERR_INVALID_ARG;
@@ -1441,9 +1512,27 @@ csrc_status csrc_create_from_coo(csrc_handle* out, int32_t n, int64_t nnz, const
 
 csrc_status csrc_partition(csrc_handle h, int32_t nbands, int32_t* band_ptr_out) {
   if (!h || nbands < 0) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   try {
-    CSRC_TRY_S(make_plan(h, nbands));
+    // the window strategy's lists are rebuilt from the new partition now, the stream-order
+    // plans when next needed
+    h->part_nbands = nbands;
+    h->owner_nbands = nbands;
+    drop_owner_plans(h);
+    free_plan(h->plan);
+    free_plan(h->plan_b1);
+    h->have_plan = h->have_b1 = false;
+    OwnerPlan* op = nullptr;
+    const csrc_status st = owner_for(h, 1, &op);
+    if (st == CSRC_ERR_NOT_PARTITIONED) {
+      // no window of this matrix fits in shared memory: report the partition all the same
+      nnz_partition(h->ia, 0, h->n, nbands > 0 ? std::min<int32_t>(nbands, std::max<int32_t>(1, h->n))
+                                               : owner_auto_bands(h, 1), h->part);
+    } else if (st != CSRC_OK) {
+      return st;
+    }
+    ++h->generation;
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
   }
@@ -1453,7 +1542,8 @@ csrc_status csrc_partition(csrc_handle h, int32_t nbands, int32_t* band_ptr_out)
 
 csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32_t* colors_out) {
   if (!h) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   const int32_t n = h->n;
   if (n == 0) {
     h->ncolors = 0;
@@ -1562,7 +1652,8 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream) {
   if (!h || !x || !y) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   if (h->n == 0) {
     h->tuned = CSRC_STRAT_WINDOW;
     return CSRC_OK;
@@ -1582,33 +1673,51 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
       CSRC_TRY(cudaEventElapsedTime(ms, e0, e1));
       return CSRC_OK;
     };
-    // band counts: the automatic choice, one band per SM, and four per SM (windows split further as needed)
-    const int32_t counts[3] = {0, h->sms, 4 * h->sms};
+    // the window strategy with the automatic band count, half and twice as many bands;
+    // then the stream-order strategies, and the colour strategy when the rows are coloured
     float best = 1e30f;
     int32_t best_nb = 0, best_st = CSRC_STRAT_WINDOW;
     csrc_status st = CSRC_OK;
+    const int32_t nb0 = h->part_nbands > 0 ? h->part_nbands : owner_auto_bands(h, 1);
+    const int32_t counts[3] = {nb0, std::max(1, nb0 / 2), nb0 * 2};
     for (int32_t nb : counts) {
-      if (nb > h->n) continue;
-      if ((st = make_plan(h, nb)) != CSRC_OK) break;
-      const csrc_strategy cands[3] = {CSRC_STRAT_WINDOW, CSRC_STRAT_ATOMIC, CSRC_STRAT_COLOR};
+      if (nb > h->n && nb != nb0) continue;
+      h->owner_nbands = nb;
+      drop_owner_plans(h);
+      OwnerPlan* op = nullptr;
+      const csrc_status ps = owner_for(h, 1, &op);
+      if (ps == CSRC_ERR_NOT_PARTITIONED) continue;
+      if ((st = ps) != CSRC_OK) break;
+      float ms = 0.f;
+      if ((st = time_it(CSRC_STRAT_WINDOW, &ms)) != CSRC_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_nb = nb;
+        best_st = CSRC_STRAT_WINDOW;
+      }
+    }
+    if (st == CSRC_OK) {
+      const csrc_strategy cands[3] = {CSRC_STRAT_WINDOW_ATOMIC, CSRC_STRAT_ATOMIC, CSRC_STRAT_COLOR};
       for (csrc_strategy c : cands) {
-        if (c == CSRC_STRAT_WINDOW && !h->plan_covers) continue;
-        if (c == CSRC_STRAT_COLOR && (h->ncolors == 0 || nb != 0)) continue;  // colouring does not use bands
+        if (c == CSRC_STRAT_COLOR && h->ncolors == 0) continue;
+        if (c != CSRC_STRAT_COLOR && !h->have_plan && (st = make_plan(h)) != CSRC_OK) break;
+        if (c == CSRC_STRAT_WINDOW_ATOMIC && !h->plan_covers) continue;
         float ms = 0.f;
         if ((st = time_it(c, &ms)) != CSRC_OK) break;
         if (ms < best) {
           best = ms;
-          best_nb = nb;
           best_st = c;
         }
       }
-      if (st != CSRC_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->profiling = prof;
     if (st != CSRC_OK) return st;
-    CSRC_TRY_S(make_plan(h, best_nb));
+    if (h->owner_nbands != best_nb) {
+      h->owner_nbands = best_nb;
+      drop_owner_plans(h);
+    }
     h->tuned = best_st;
     ++h->generation;
     return CSRC_OK;
@@ -1619,7 +1728,8 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
 
 csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream) {
   if (!h || !X || !Y || nrhs <= 0 || h->rect()) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   if (h->n == 0 || nrhs == 1) return CSRC_OK;
   try {
     const bool prof = h->profiling;
@@ -1630,12 +1740,11 @@ csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nr
     float best = 1e30f;
     int32_t best_rk = 0;
     csrc_status st = CSRC_OK;
-    for (int32_t rk = 2; rk <= 8 && st == CSRC_OK; rk *= 2) {
+    for (int32_t rk = 1; rk <= 8 && st == CSRC_OK; rk *= 2) {
       if (rk > nrhs) break;
-      DevPlan* p = nullptr;
-      bool covers = false;
-      const csrc_status ps = plan_for(h, rk, &p, &covers);
-      if (ps == CSRC_ERR_NOT_PARTITIONED || (ps == CSRC_OK && !covers)) break;  // wider passes fit even less
+      OwnerPlan* p = nullptr;
+      const csrc_status ps = owner_for(h, rk, &p);
+      if (ps == CSRC_ERR_NOT_PARTITIONED) break;  // wider passes fit even less
       if (ps != CSRC_OK) {
         st = ps;
         break;
@@ -1675,7 +1784,8 @@ csrc_status csrc_set_profiling(csrc_handle h, int32_t enable) {
 csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out) {
   if (!h || !out) return CSRC_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   csrc_status st = CSRC_OK;
   for (auto& t : h->timed) {
     float ms = 0.f;
@@ -1706,7 +1816,8 @@ csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_
   const char* xa = static_cast<const char*>(x);
   if (ba < xa + vb && xa < ba + vb) return CSRC_ERR_ALIAS;
   if (n == 0) return CSRC_OK;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   const bool fp64 = h->xbytes() == 8;
   const int nb = solver_blocks(h->sms);
   if (!h->d_solve) CSRC_TRY(cudaMalloc(&h->d_solve, 6 * vb));
@@ -1780,7 +1891,9 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
   info->storage = h->storage;
   info->arith = h->arith;
   const int64_t vb = (int64_t)h->vbytes(), xb = (int64_t)h->xbytes();
-  const int64_t ib = h->have_plan && h->plan.jslot16 ? 2 : 4;  // index bytes per pair
+  // index bytes per pair: 2 with index compression (unless a stream-order plan had to keep
+  // 32-bit slots because a window exceeds 65,536 rows)
+  const int64_t ib = (h->flags & CSRC_FLAG_COMPRESS_INDICES) && (!h->have_plan || h->plan.jslot16) ? 2 : 4;
   info->model_bytes = 4 * ((int64_t)h->n + 1) + ib * h->h + (h->sym ? 1 : 2) * vb * h->h + vb * h->n + 2 * xb * h->n;
   if (h->have_plan) {
     info->nbands = h->plan.nb;
@@ -1791,6 +1904,25 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
     info->accum_bytes = h->plan.spill * (2 * xb + 4) + h->plan.nacc * (8 + 2 * xb);
     info->max_window_slots = h->plan.max_slots;
     info->smem_bytes = h->plan.smem_bytes;
+    info->stream_nbands = h->plan.nb;
+    info->stream_spill_entries = h->plan.spill;
+  }
+  if (h->have_oplan) {  // the window strategy's plan: its figures take precedence
+    const OwnerPlan& p = h->oplan;
+    info->nbands = p.nb;
+    info->page_rows = 0;
+    info->spill_entries = p.spill;
+    info->spill_rows = p.nacc;
+    info->accum_bytes = p.spill * (2 * xb + 4) + p.nacc * (8 + 2 * xb);
+    info->max_window_slots = p.max_slots;
+    info->smem_bytes = p.smem_bytes;
+    info->list_entries = p.entries;
+    info->list_slices = p.nslices;
+    info->list_lane_steps = p.lane_steps;
+    // what the owner kernel moves: slots and values of the entries, lane words and slice
+    // offsets, band records, spill row list, x of every window slot, y and the spill writes
+    info->list_bytes = (2 + vb) * p.entries + (4 * kOwnerLanes + 8) * p.nslices + 20 * (int64_t)p.nb +
+                       4 * p.spill + xb * ((int64_t)h->n + p.spill) + xb * h->n + xb * p.spill;
   }
   info->ncolors = h->ncolors;
   info->tuned_strategy = h->tuned;
@@ -1807,7 +1939,8 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
 
 csrc_status csrc_get_last_device_error(csrc_handle h) {
   if (!h) return CSRC_ERR_INVALID_ARG;
-  CSRC_TRY_S(ensure_device(h));
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
   CSRC_TRY(cudaDeviceSynchronize());
   int32_t w = 0;
   CSRC_TRY(cudaMemcpy(&w, h->d_status, 4, cudaMemcpyDeviceToHost));
@@ -1821,10 +1954,12 @@ csrc_status csrc_get_last_device_error(csrc_handle h) {
 csrc_status csrc_destroy(csrc_handle h) {
   if (!h) return CSRC_OK;
   drop_batches_of(h);
-  ensure_device(h);
+  DeviceGuard dg;
+  dg.enter(h);
   cudaDeviceSynchronize();
   free_plan(h->plan);
-  for (int i = 0; i < 3; ++i) free_plan(h->plan_rk[i]);
+  drop_owner_plans(h);
+  free_owner_plan(h->oplan_bt);
   free_plan(h->plan_b1);
   free_plan(h->plan_bt);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);

@@ -149,6 +149,96 @@ struct DevPlan {
   uint16_t* jslot16 = nullptr;   // the same slots as 16 bits (index compression); jslot is then null
 };
 
+// ---------------------------------------------------------------------------- owner lists
+// The window strategy's plan (owner.cu, owner_plan.cpp). Each band [r0, r1) of the
+// Section 3.1 partition writes the rows of its effective range: its own rows and the
+// rows below r0 that its pairs scatter into ("spill rows"). Window slots number them:
+// slots [0, nspill) are the spill rows in ascending order, slots [nspill, nspill + nown)
+// the own rows. Every slot has an entry list, each entry a (value, slot) couple whose
+// product value * x[slot] belongs to the slot's row:
+//   own row r:  the diagonal ad[r] (with x of r), the row's lower pairs al[k] (with x of
+//               ja[k]) in column order, then the pairs of later rows i of the band with
+//               ja[k] = r, au[k] (with x of i), in row order;
+//   spill row:  the pairs of the band that scatter into it, au[k] with x of their row.
+// A^T x uses the same lists with al and au exchanged (Section 5). The scatter of Fig. 2(a)
+// is thereby sorted by target when the plan is built, and each slot's sum is formed by one
+// lane in registers: no two lanes ever add into the same window row.
+// The lists of a band are stored in jagged-diagonal order: slots are sorted by list length
+// (descending), cut into slices of 32 (one lane each), and step m of a slice holds entry m
+// of every lane whose list is longer than m, contiguously, so that a warp's loads of one
+// step are coalesced.
+constexpr int kOwnerLanes = 32;
+constexpr uint32_t kOwnerPadSlot = 0xffffu;  // lane word slot of an unused lane (length 0)
+constexpr int kOwnerMaxSlots = 65535;         // slots are 16-bit; 0xffff marks unused lanes
+constexpr int kOwnerMaxLength = 65535;        // list lengths are 16-bit
+
+// Kernel shape: threads per CTA and CTAs per SM the window budget is sized for.
+constexpr int kOwnerThreads = 256;
+inline int owner_ctas_per_sm(int rk) { return rk <= 1 ? 4 : (rk <= 2 ? 2 : 1); }
+inline int owner_smem_budget(int rk) { return smem_limit_for(owner_ctas_per_sm(rk)); }
+
+struct OwnerPlan {
+  int32_t nb = 0;            // bands
+  int32_t rk = 1;            // columns per pass the windows are sized for
+  int64_t entries = 0;       // list entries of all bands (n + 2h)
+  int64_t lane_steps = 0;    // sum over slices of 32 * longest list (FMA lanes issued)
+  int64_t nslices = 0;
+  int64_t spill = 0;         // spill slots of all bands
+  int32_t max_slots = 0;
+  int32_t smem_bytes = 0;    // window bytes of the largest band (rk columns)
+  int4* band = nullptr;          // nb: {r0, own rows, spill rows, first spill slot}
+  int32_t* band_slice = nullptr; // nb+1: slices of band b are [band_slice[b], band_slice[b+1])
+  int64_t* slice_off = nullptr;  // nslices: first entry of each slice
+  uint32_t* lane = nullptr;      // nslices*32: (list length << 16) | slot
+  int32_t* spill_row = nullptr;  // spill: the row of every spill slot
+  uint16_t* S = nullptr;         // entries: the slot whose x the entry multiplies
+  void* VA = nullptr;            // entries: values for A x (storage type)
+  void* VT = nullptr;            // entries: values for A^T x (VA itself when al = au)
+  // accumulation (spill -> y) map, rows ascending, sources in band order
+  int64_t nacc = 0;
+  int32_t* acc_row = nullptr;
+  int32_t* acc_ptr = nullptr;
+  int32_t* acc_src = nullptr;
+  void* spill_buf = nullptr;     // spill values (rk per slot; double or float)
+  std::vector<int64_t> band_entries;  // host copy: list entries of each band (batched scheduling)
+};
+
+// Arguments of one owner-kernel launch (passed by value).
+struct OwnerArgs {
+  const int4* band;
+  const int32_t* band_slice;
+  const int64_t* slice_off;
+  const uint32_t* lane;
+  const int32_t* spill_row;
+  const uint16_t* S;
+  const void* V;
+  const void* x;
+  void* y;
+  void* spill;
+  int32_t ldx;        // row stride of x and y in elements (the pass's columns start at x, y)
+  int32_t band_offset;
+};
+
+// Host side of the owner plan (owner_plan.cpp). Builds the lists of the bands of `part`
+// (split further while a window of rk columns of `slot_bytes` bytes each would exceed
+// `budget` bytes or 65,535 slots), the accumulation map, and uploads them; values are
+// gathered on the device from al / au / ad (storage type of vbytes bytes per value).
+// Returns CSRC_ERR_NOT_PARTITIONED when a list is longer than 65,535 entries or a single
+// row's window does not fit.
+csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& ia, const std::vector<int32_t>& ja,
+                             const std::vector<int32_t>& part, int rk, int slot_bytes, int budget, int vbytes,
+                             int spill_bytes, const void* al, const void* au, const void* ad, bool sym,
+                             OwnerPlan& out);
+void free_owner_plan(OwnerPlan& p);
+
+// Launchers (owner.cu).
+cudaError_t prepare_owner_kernels();
+// out_a[e] / out_t[e] = the value of entry e for A x / A^T x, from its source code
+// (k << 2 | kind, kind 0 = ad[k], 1 = al[k], 2 = au[k]); vbytes = 8, 4 or 2.
+cudaError_t launch_owner_gather(int vbytes, const int64_t* code, int64_t count, const void* al, const void* au,
+                                const void* ad, void* out_a, void* out_t, cudaStream_t s);
+cudaError_t launch_owner(int storage, int rk, const OwnerArgs& a, int nbands, int smem, cudaStream_t s);
+
 // Arguments of the band kernels (passed by value).
 struct BandArgs {
   int32_t n;
@@ -198,7 +288,6 @@ enum : int32_t { DEV_RANGE = 1, DEV_TIMEOUT = 2, DEV_BOUNDS = 4 };
 // Launchers (kernels.cu). All return cudaGetLastError() of their launch.
 cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandArgs& a, int nbands,
                         int smem_bytes, cudaStream_t s);
-cudaError_t launch_band_rk(Arith arith, int storage, const BandArgs& a, int nbands, int smem, cudaStream_t s);
 cudaError_t launch_accumulate(Arith arith, int storage, int64_t nacc, int rk, int ldx, const int32_t* acc_row,
                               const int32_t* acc_ptr, const int32_t* acc_src, const void* spill, void* y,
                               cudaStream_t s);
@@ -225,7 +314,6 @@ cudaError_t launch_solver_op(int op, bool fp64, int64_t n, int nblocks, double s
 // nothing arrives at and ORs DEV_TIMEOUT into *status.
 cudaError_t launch_wait_probe(long long limit, int32_t* status, cudaStream_t s);
 cudaError_t prepare_band_kernels();
-cudaError_t prepare_band_kernels_rk();
 cudaError_t prepare_band_kernels_block();
 cudaError_t launch_band_block(Arith arith, int storage, const BandArgs& a, int nbands, int smem, cudaStream_t s);
 

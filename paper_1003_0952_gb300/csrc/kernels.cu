@@ -1,4 +1,4 @@
-// Single-vector band kernels (RK = 1) and the accumulation kernel of the CSRC
+// Stream-order band kernels (single vectors) and the accumulation kernel of the CSRC
 // products. The band kernel itself is in band.cuh.
 #include "band.cuh"
 
@@ -80,7 +80,6 @@ cudaError_t prepare_band_kernels() {
   if ((r = set_smem_mode<MODE_F64>()) != cudaSuccess) e = r;
   if ((r = set_smem_mode<MODE_F32>()) != cudaSuccess) e = r;
   if ((r = set_smem_mode<MODE_BF16>()) != cudaSuccess) e = r;
-  if ((r = prepare_band_kernels_rk()) != cudaSuccess) e = r;
   if ((r = prepare_band_kernels_block()) != cudaSuccess) e = r;
   return e;
 }
@@ -103,7 +102,6 @@ static void launch_mode(int group, bool atomic, const BandArgs& a, dim3 grid, in
 cudaError_t launch_band(Arith arith, int storage, bool atomic_flush, const BandArgs& a, int nbands, int smem,
                         cudaStream_t s) {
   if (nbands <= 0) return cudaSuccess;
-  if (a.rk > 1) return launch_band_rk(arith, storage, a, nbands, smem, s);
   if (a.block > 1) return launch_band_block(arith, storage, a, nbands, smem, s);
   const int mode = mode_of(arith, storage);
   dim3 grid(nbands);

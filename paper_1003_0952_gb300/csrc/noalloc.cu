@@ -21,8 +21,8 @@
 namespace {
 
 // Spilled partial sums of one product: CSRC_NOALLOC_MAX_SPILL_ENTRIES values
-// (doubles for FP64 storage, floats otherwise). 16 MiB, held by every GPU that
-// loads the library until the process exits.
+// (doubles for FP64 storage; floats otherwise, which use the first half of the
+// array). 16 MiB, held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_noalloc_spill[CSRC_NOALLOC_MAX_SPILL_ENTRIES];
 
 constexpr int kMaxDevices = 64;
@@ -56,9 +56,11 @@ extern "C" csrc_status csrc_spmv_noalloc(csrc_handle h, const void* x, void* y, 
   if (cudaGetDevice(&cur) != cudaSuccess) return CSRC_ERR_CUDA;
   if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return CSRC_ERR_CUDA;
   void* spill = nullptr;
-  const csrc_status st = scratch_address(dev, &spill);
-  if (st != CSRC_OK) return st;
-  // Every spill slot that the accumulation kernel reads is written by the band
+  csrc_status st = scratch_address(dev, &spill);
+  // Every spill slot that the accumulation kernel reads is written by the product
   // kernel of the same call, so nothing in the array has to start at zero.
-  return csrc::spmv_external_spill(h, x, y, transpose != 0, spill, CSRC_NOALLOC_MAX_SPILL_ENTRIES, stream);
+  if (st == CSRC_OK)
+    st = csrc::spmv_external_spill(h, x, y, transpose != 0, spill, CSRC_NOALLOC_MAX_SPILL_ENTRIES, stream);
+  if (cur != dev) cudaSetDevice(cur);  // the caller's current device, as it was
+  return st;
 }

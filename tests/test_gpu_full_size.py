@@ -51,7 +51,7 @@ def test_q1_fp64_all_strategies(cs, name):
     try:
         cs.csrc_partition(h, 0)
         cs.csrc_color(h, 12345)
-        for strategy in ("window", "atomic", "color"):
+        for strategy in ("window", "window_atomic", "atomic", "color"):
             for tr in (False, True):
                 err = oracle.max_rel_err(m, x, _product(cs, h, x, "f64", strategy, tr), refs[tr], transpose=tr)
                 print(f"{name} f64 {strategy} transpose={tr}: max rel err {err:.3e}")

@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
-STRATS = ("window", "atomic", "color")
+STRATS = ("window", "window_atomic", "atomic", "color")
 
 
 @pytest.fixture(scope="module")
@@ -91,17 +91,53 @@ def test_p1_grid_fp64(cs, strategy, transpose):
         h.close()
 
 
-@pytest.mark.parametrize("strategy", ["window", "atomic"])
-def test_fp64_pipe_arithmetic_flag(cs, strategy):
+@pytest.mark.parametrize("strategy", ["window", "window_atomic", "atomic"])
+@pytest.mark.parametrize("flags", ["default", "fp64", "df32"])
+def test_arithmetic_flags(cs, strategy, flags):
+    # FP64 storage computes on the FP64 pipe unless double-float is asked for, which only the
+    # stream-order strategies use
     m = fe.p1_grid(60, 50, 11)
     x = fe.source_vector(m.n, 12)
-    h = Handle(cs, m, flags=cs.CSRC_FLAG_FP64_ARITH)
+    f = {"default": 0, "fp64": cs.CSRC_FLAG_FP64_ARITH, "df32": cs.CSRC_FLAG_DF32_ARITH}[flags]
+    h = Handle(cs, m, flags=f)
     try:
-        assert cs.csrc_get_info(h.h)["arith"] == 1
+        assert cs.csrc_get_info(h.h)["arith"] == (0 if flags == "df32" else 1)
         for tr in (False, True):
             _check(m, x, h.run(x, strategy, tr), tr, TOL["f64"])
     finally:
         h.close()
+
+
+def test_window_strategy_is_bitwise_reproducible(cs):
+    # every window row is summed by one lane in a fixed order: repeated products agree bit
+    # for bit, for every storage type and for A x and A^T x
+    m = fe.q1_hex(12, 3, 91)
+    x = fe.source_vector(m.n, 92)
+    for storage in ("f64", "f32", "bf16"):
+        h = Handle(cs, m, storage)
+        try:
+            for tr in (False, True):
+                y0 = h.run(x, "window", tr)
+                for _ in range(3):
+                    np.testing.assert_array_equal(h.run(x, "window", tr), y0)
+        finally:
+            h.close()
+
+
+def test_window_lists_cover_every_entry(cs):
+    # the lists hold every stored value once (n diagonal entries and both values of each pair)
+    for m in (fe.q1_hex(12, 3, 93), fe.p1_grid(70, 40, 94), fe.tet_mesh(5000, 95, method="kuhn")):
+        x = fe.source_vector(m.n, 96)
+        h = Handle(cs, m)
+        try:
+            for nb in (None, 1, 5, 300):
+                h.run(x, "window", False, nbands=nb)
+                info = cs.csrc_get_info(h.h)
+                assert info["list_entries"] == m.nnz
+                assert info["list_lane_steps"] >= info["list_entries"]
+                assert info["list_slices"] * 32 >= m.n + info["spill_entries"]
+        finally:
+            h.close()
 
 
 # --------------------------------------------------------------------------- exact integer cases
@@ -141,7 +177,7 @@ def test_q1_vector_many_bands(cs, nbands):
     x = fe.source_vector(m.n, 22)
     h = Handle(cs, m)
     try:
-        for strategy in ("window", "atomic"):
+        for strategy in ("window", "window_atomic", "atomic"):
             for tr in (False, True):
                 _check(m, x, h.run(x, strategy, tr, nbands=nbands), tr, TOL["f64"])
         info = cs.csrc_get_info(h.h)
@@ -214,7 +250,7 @@ def test_long_rows_run_sixteen_lanes(cs, storage):
     h, hi = Handle(cs, m, storage), Handle(cs, mi, storage)
     try:
         for nbands in (None, 7, 300):
-            for strategy in ("window", "atomic"):
+            for strategy in ("window", "window_atomic", "atomic"):
                 for tr in (False, True):
                     _check(m, x, h.run(x, strategy, tr, nbands=nbands), tr, TOL[storage])
                     np.testing.assert_array_equal(hi.run(xi, strategy, tr, nbands=nbands), _ref(mi, xi, tr))
@@ -237,7 +273,9 @@ def test_symmetric_values(cs):
     try:
         # colour-ordered rows have a fixed update order: A x and A^T x agree bit for bit
         np.testing.assert_array_equal(h.run(x, "color", False), h.run(x, "color", True))
-        for s in ("window", "atomic"):
+        # so do the window strategy's lists (one lane per row, a fixed order)
+        np.testing.assert_array_equal(h.run(x, "window", False), h.run(x, "window", True))
+        for s in ("window", "window_atomic", "atomic"):
             y1, y2 = h.run(x, s, False), h.run(x, s, True)
             _check(m, x, y1, False, TOL["f64"])
             assert oracle.max_rel_err(m, x, y1, y2) <= 1e-12
@@ -289,7 +327,7 @@ def test_symmetric_value_storage_other_paths(cs):
     h = Handle(cs, m, flags=flags | cs.CSRC_FLAG_NODE_BLOCKS)
     try:
         x = fe.source_vector(m.n, 59)
-        _check(m, x, h.run(x, "window", False), False, TOL["f64"])
+        _check(m, x, h.run(x, "window_atomic", False), False, TOL["f64"])
         assert cs.csrc_get_info(h.h)["block"] == 3
     finally:
         h.close()
@@ -404,29 +442,36 @@ def test_double_float_range_is_reported(cs):
     m = fe.p1_grid(20, 20, 2)
     x = fe.source_vector(m.n, 3)
     x[17] = 1e300
-    h = Handle(cs, m)
+    h = Handle(cs, m, flags=cs.CSRC_FLAG_DF32_ARITH)
     try:
         xd = torch.from_numpy(x).cuda()
         yd = torch.empty_like(xd)
-        cs.csrc_spmv(h.h, xd, yd, cs.CSRC_STRAT_WINDOW)
+        cs.csrc_spmv(h.h, xd, yd, cs.CSRC_STRAT_WINDOW_ATOMIC)
         torch.cuda.synchronize()
         assert cs.csrc_get_last_device_error(h.h) == cs.CSRC_ERR_RANGE
         assert cs.csrc_get_last_device_error(h.h) == cs.CSRC_OK  # cleared by the read
-    finally:
-        h.close()
-    # FP64-pipe arithmetic handles the full double range
-    h = Handle(cs, m, flags=cs.CSRC_FLAG_FP64_ARITH)
-    try:
+        # the window strategy computes in FP64 whatever the flag
         _check(m, x, h.run(x, "window"), False, TOL["f64"])
     finally:
         h.close()
-    # matrix values outside the double-float range switch the handle to FP64 arithmetic
+    # FP64 arithmetic (the default) handles the full double range, tiny entries included
+    x2 = x.copy()
+    x2[5:40] *= 1e-20
+    x2[60:90] *= 1e20
+    h = Handle(cs, m)
+    try:
+        for s in ("window", "window_atomic", "atomic"):
+            for xx in (x, x2):
+                _check(m, xx, h.run(xx, s), False, TOL["f64"])
+    finally:
+        h.close()
+    # matrix values outside the double-float range switch a double-float handle to FP64 arithmetic
     m2 = fe.FEMatrix(m.n, m.row_ptr, m.col, m.val * 1e-30)
-    h = Handle(cs, m2)
+    h = Handle(cs, m2, flags=cs.CSRC_FLAG_DF32_ARITH)
     try:
         assert cs.csrc_get_info(h.h)["arith"] == 1
         x2 = fe.source_vector(m.n, 4)
-        _check(m2, x2, h.run(x2, "window"), False, TOL["f64"])
+        _check(m2, x2, h.run(x2, "window_atomic"), False, TOL["f64"])
     finally:
         h.close()
 
@@ -502,7 +547,8 @@ def test_autotune_picks_a_strategy_and_stays_correct(cs):
         yd = torch.empty_like(xd)
         cs.csrc_autotune(h.h, xd, yd, torch.cuda.current_stream())
         info = cs.csrc_get_info(h.h)
-        assert info["tuned_strategy"] in (cs.CSRC_STRAT_WINDOW, cs.CSRC_STRAT_COLOR, cs.CSRC_STRAT_ATOMIC)
+        assert info["tuned_strategy"] in (cs.CSRC_STRAT_WINDOW, cs.CSRC_STRAT_COLOR, cs.CSRC_STRAT_ATOMIC,
+                                          cs.CSRC_STRAT_WINDOW_ATOMIC)
         for tr in (False, True):
             _check(m, x, h.run(x, "auto", tr), tr, TOL["f64"])
     finally:
@@ -523,8 +569,9 @@ def test_node_block_kernel_matches_plain_rows_and_oracle(cs, ndof):
         hp = Handle(cs, im, storage)
         try:
             for tr in (False, True):
-                yb = hb.run(xi, "window", tr)
+                yb = hb.run(xi, "window_atomic", tr)
                 np.testing.assert_array_equal(yb, _ref(im, xi, tr))
+                np.testing.assert_array_equal(hp.run(xi, "window_atomic", tr), yb)
                 np.testing.assert_array_equal(hp.run(xi, "window", tr), yb)
             assert cs.csrc_get_info(hb.h)["block"] == ndof
             assert cs.csrc_get_info(hp.h)["block"] == 1
@@ -535,7 +582,7 @@ def test_node_block_kernel_matches_plain_rows_and_oracle(cs, ndof):
     try:
         for nb in (1, 5, 152):
             for tr in (False, True):
-                _check(m, x, h.run(x, "window", tr, nbands=nb), tr, TOL["f64"])
+                _check(m, x, h.run(x, "window_atomic", tr, nbands=nb), tr, TOL["f64"])
         # the atomic strategy runs plain rows on a second plan
         _check(m, x, h.run(x, "atomic"), False, TOL["f64"])
     finally:

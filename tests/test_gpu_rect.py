@@ -61,7 +61,7 @@ def test_rectangular_products_match_oracle(cs, storage):
             assert info["m"] == a.m and info["n"] == a.n
             assert info["rect_nnz"] == len(r.jar) > 0
             cs.csrc_color(h, 7)
-            for strategy in ("window", "atomic", "color"):
+            for strategy in ("window", "window_atomic", "atomic", "color"):
                 y = _run(cs, h, a, x, storage, strategy, False)
                 e = oracle.max_rel_err_rect(a.n, a.m, a.row_ptr, a.col, a.val, x, y, y_ref)
                 assert e <= TOL[storage], (a.name, strategy, e)
@@ -83,7 +83,7 @@ def test_rectangular_integer_values_bit_exact(cs, storage):
     try:
         for nbands in (0, 5, 200):
             cs.csrc_partition(h, nbands)
-            for strategy in ("window", "atomic"):
+            for strategy in ("window", "window_atomic", "atomic"):
                 np.testing.assert_array_equal(_run(cs, h, ai, x, storage, strategy, False), oracle.csrcr_spmv(r, x))
                 np.testing.assert_array_equal(_run(cs, h, ai, xt, storage, strategy, True),
                                               oracle.csrcr_spmv_t(r, xt))

@@ -45,7 +45,7 @@ def _solve(cs, h, b, storage, rtol, maxit, strategy="window", x0=None):
     return res, xd.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("strategy", ["window", "atomic", "color"])
+@pytest.mark.parametrize("strategy", ["window", "window_atomic", "atomic", "color"])
 def test_bicg_fp64_matches_oracle(cs, strategy):
     for m in (fe.q1_hex(10, 3, 101), fe.tet_mesh(6000, 102, method="kuhn")):
         c = oracle.from_matrix(m)

@@ -218,7 +218,7 @@ def test_autotune_spmm_k_tile(cs):
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.empty_like(Xd)
         cs.csrc_autotune_spmm(h, Xd, Yd, 16, torch.cuda.current_stream())
-        assert cs.csrc_get_info(h)["tuned_rk"] in (2, 4, 8)
+        assert cs.csrc_get_info(h)["tuned_rk"] in (1, 2, 4, 8)
         Y = _run(cs, h, X, "f64", False)
         assert oracle.max_rel_err(m, X, Y, oracle.csrc_spmm(c, X)) <= 1e-12
     finally:

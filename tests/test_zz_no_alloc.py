@@ -5,8 +5,9 @@ another allocator's pool, or their host thread must not block on the device
 synchronisation that allocation can cause. They create and partition a handle once,
 then call csrc_spmv_noalloc, whose spill buffer is a fixed array in the library's
 static device memory. These tests call it through the C ABI and check that two calls
-in a row give what csrc_spmv / csrc_spmv_t give with the window strategy, within the
-FP64 tolerance of the parity tests (1e-12 relative to sum_j |a_ij||x_j| per row).
+in a row give what csrc_spmv / csrc_spmv_t give with the window strategy, and what the
+CPU oracle gives, within the tolerances of the parity tests (relative to
+sum_j |a_ij||x_j| per row: 1e-12 for FP64 storage, 1e-5 for FP32, 1e-2 for BF16).
 
 The file is named so that pytest collects it last.
 """
@@ -46,15 +47,21 @@ def _create(cs, m, storage="f64"):
     return h
 
 
-def test_two_calls_match_the_window_product(cs):
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_two_calls_match_the_window_product(cs, storage):
     m = fe.q1_hex(14, 3, 21)  # n = 8232, RCM order: several bands, spilled rows
-    h = _create(cs, m)
+    h = _create(cs, m, storage)
+    tol = {"f64": TOL, "f32": 1e-5, "bf16": 1e-2}[storage]
+    dt = torch.float64 if storage == "f64" else torch.float32
+    c = oracle.from_matrix(m)
     try:
         info = cs.csrc_get_info(h)
         assert 0 < info["spill_entries"] <= cs.CSRC_NOALLOC_MAX_SPILL_ENTRIES
         s = torch.cuda.current_stream()
-        x1 = torch.from_numpy(fe.source_vector(m.n, 31)).cuda()
-        x2 = torch.from_numpy(fe.source_vector(m.n, 32)).cuda()
+        xs = [fe.source_vector(m.n, 31), fe.source_vector(m.n, 32)]
+        if storage != "f64":  # the vectors the product sees are FP32
+            xs = [v.astype(np.float32).astype(np.float64) for v in xs]
+        x1, x2 = (torch.as_tensor(v, dtype=dt).cuda() for v in xs)
         y = torch.full_like(x1, float("nan"))
         yref = torch.full_like(x1, float("nan"))
         mt = _transpose(m)
@@ -66,9 +73,14 @@ def test_two_calls_match_the_window_product(cs):
             cs.csrc_spmv_noalloc(h, x, y, tr, s)
             torch.cuda.synchronize()
             assert cs.csrc_get_last_device_error(h) == cs.CSRC_OK
-            xn = x.cpu().numpy()
-            err = oracle.max_rel_err(mt if tr else m, xn, y.cpu().numpy(), yref.cpu().numpy())
-            assert err <= TOL, (tr, err)
+            xn = x.cpu().numpy().astype(np.float64)
+            yn = y.cpu().numpy().astype(np.float64)
+            err = oracle.max_rel_err(mt if tr else m, xn, yn, yref.cpu().numpy().astype(np.float64))
+            assert err <= tol, (tr, err)
+            # and against the CPU oracle itself, so that a fault shared by both GPU paths shows
+            ref = (oracle.csrc_spmv_t if tr else oracle.csrc_spmv)(c, xn)
+            err = oracle.max_rel_err(mt if tr else m, xn, yn, ref)
+            assert err <= tol, (tr, "oracle", err)
     finally:
         cs.csrc_destroy(h)
 
