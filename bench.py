@@ -182,6 +182,8 @@ def describe(name: str, m) -> dict:
         "q1v_96": "Q1 hex 27-point stencil, 96^3 nodes x 3 DOF (3x3 blocks), random then RCM order, "
                   "al != au U[-1,1], FP64 values, y = A x and y = A^T x",
         "q1s_96": "Q1 hex 27-point stencil, 96^3 nodes, scalar, random then RCM order, FP64, y = A x and y = A^T x",
+        "q1v_64": "Q1 hex 27-point stencil, 64^3 nodes x 3 DOF (3x3 blocks), random then RCM order, FP64, "
+                  "y = A x and y = A^T x (profiling case)",
         "p1_100x100": "P1 triangles on a 100x100 node grid, natural order, FP64, y = A x and y = A^T x",
     }.get(name, name), "n": int(m.n), "nnz": int(m.nnz), "pairs": int(m.pairs),
         "strategy": "window (shared-memory windows + deterministic accumulation)",

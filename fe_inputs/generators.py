@@ -465,6 +465,9 @@ CONFIGS = {
     "p1_100x100": (lambda: p1_grid(100, 100, 1001), 2001),
     "q1s_96": (lambda: q1_hex(96, 1, 1002), 2002),
     "q1v_96": (lambda: q1_hex(96, 3, 1002), 2002),
+    # the same structure on 64^3 nodes (n = 786,432, nnz = 62.4M): a smaller case of q1v_96's
+    # kernels for profiler captures (still several times larger than L2)
+    "q1v_64": (lambda: q1_hex(64, 3, 1002), 2002),
     "tet_delaunay_2m": (lambda: tet_mesh(2_000_000, 1003), 2003),
     "q1s_96_multi": (lambda: q1_hex(96, 1, 1002), 2004),
     "batch_256": (lambda: batch_meshes(256, 1005), 2005),

@@ -522,7 +522,7 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
 // Automatic band count of an owner plan: a multiple of the CTAs the GPU holds at once
 // (SMs x resident CTAs for rk columns), with about kOwnerBandNnz non-zeros per band, so
 // that the bands of equal weight finish in whole waves.
-constexpr int64_t kOwnerBandNnz = 80000;
+constexpr int64_t kOwnerBandNnz = 100000;
 int32_t owner_auto_bands(const csrc_matrix_s* h, int rk) {
   const int64_t nnz = (int64_t)h->n + 2 * h->h;
   const int64_t slots = (int64_t)h->sms * owner_ctas_per_sm(rk);
@@ -746,6 +746,7 @@ OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y,
   a.slice_off = p.slice_off;
   a.lane = p.lane;
   a.spill_row = p.spill_row;
+  a.spill_pos = p.spill_pos;
   a.S = p.S;
   a.V = transpose ? p.VT : p.VA;
   a.x = x;
@@ -764,7 +765,7 @@ csrc_status run_owner(csrc_matrix_s* h, const OwnerPlan& p, bool transpose, cons
                         [&] { return launch_owner(h->storage, rk, a, p.nb, p.smem_bytes, s); }));
   if (p.nacc > 0)
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
-      return launch_accumulate(h->arith, h->storage, p.nacc, rk, ldx, p.acc_row, p.acc_ptr, p.acc_src, spill, y, s);
+      return launch_accumulate(h->arith, h->storage, p.nacc, rk, ldx, p.acc_row, p.acc_ptr, nullptr, spill, y, s);
     }));
   return CSRC_OK;
 }
@@ -1318,7 +1319,7 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   const OwnerArgs a = owner_args(p, transpose, x, y, spill, 1);
   CSRC_TRY(launch_owner(h->storage, 1, a, p.nb, p.smem_bytes, s));
   if (p.nacc > 0)
-    CSRC_TRY(launch_accumulate(h->arith, h->storage, p.nacc, 1, 1, p.acc_row, p.acc_ptr, p.acc_src, spill, y, s));
+    CSRC_TRY(launch_accumulate(h->arith, h->storage, p.nacc, 1, 1, p.acc_row, p.acc_ptr, nullptr, spill, y, s));
   return CSRC_OK;
 }
 

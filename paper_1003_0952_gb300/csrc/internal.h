@@ -191,14 +191,16 @@ struct OwnerPlan {
   int64_t* slice_off = nullptr;  // nslices: first entry of each slice
   uint32_t* lane = nullptr;      // nslices*32: (list length << 16) | slot
   int32_t* spill_row = nullptr;  // spill: the row of every spill slot
+  int32_t* spill_pos = nullptr;  // spill: where the slot's sum goes in the spill buffer, which is
+                                 // ordered by receiving row (and by band within a row)
   uint16_t* S = nullptr;         // entries: the slot whose x the entry multiplies
   void* VA = nullptr;            // entries: values for A x (storage type)
   void* VT = nullptr;            // entries: values for A^T x (VA itself when al = au)
-  // accumulation (spill -> y) map, rows ascending, sources in band order
+  // accumulation (spill -> y): receiving rows ascending; the sums of row acc_row[i] are
+  // spill entries [acc_ptr[i], acc_ptr[i+1]), in band order
   int64_t nacc = 0;
   int32_t* acc_row = nullptr;
   int32_t* acc_ptr = nullptr;
-  int32_t* acc_src = nullptr;
   void* spill_buf = nullptr;     // spill values (rk per slot; double or float)
   std::vector<int64_t> band_entries;  // host copy: list entries of each band (batched scheduling)
 };
@@ -210,6 +212,7 @@ struct OwnerArgs {
   const int64_t* slice_off;
   const uint32_t* lane;
   const int32_t* spill_row;
+  const int32_t* spill_pos;
   const uint16_t* S;
   const void* V;
   const void* x;

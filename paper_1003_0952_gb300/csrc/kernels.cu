@@ -6,7 +6,9 @@ namespace csrc {
 
 // ---------------------------------------------------------------------------- accumulation
 // y[row, c] += sum of the row's spilled partial sums, in band order (deterministic).
-// One thread per (receiving row, column); spill entries hold rk columns each.
+// One thread per (receiving row, column); spill entries hold rk columns each. Row i's sums
+// are spill entries acc_src[e] for e in [acc_ptr[i], acc_ptr[i+1]), or the entries e
+// themselves when acc_src is null (a spill buffer already ordered by receiving row).
 template <typename T>
 __global__ void accumulate_kernel(int64_t nacc, int rk, int ldx, const int32_t* __restrict__ acc_row,
                                   const int32_t* __restrict__ acc_ptr, const int32_t* __restrict__ acc_src,
@@ -18,7 +20,11 @@ __global__ void accumulate_kernel(int64_t nacc, int rk, int ldx, const int32_t* 
   const int row = acc_row[i];
   T s = y[(size_t)row * ldx + c];
   const int e1 = acc_ptr[i + 1];
-  for (int e = acc_ptr[i]; e < e1; ++e) s += spill[(size_t)acc_src[e] * rk + c];
+  if (acc_src) {
+    for (int e = acc_ptr[i]; e < e1; ++e) s += spill[(size_t)acc_src[e] * rk + c];
+  } else {
+    for (int e = acc_ptr[i]; e < e1; ++e) s += spill[(size_t)e * rk + c];
+  }
   y[(size_t)row * ldx + c] = s;
 }
 

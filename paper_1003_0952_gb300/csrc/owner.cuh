@@ -60,8 +60,82 @@ __device__ __forceinline__ double owner_ldv(const double* p) { return __ldg(p); 
 __device__ __forceinline__ float owner_ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ uint16_t owner_ldv(const uint16_t* p) { return __ldg(p); }
 
-// Entries loaded per lane before their multiply-adds (their load latencies overlap).
-constexpr int owner_unroll(int rk) { return rk == 1 ? 8 : (rk == 2 ? 4 : 2); }
+// Loads of steps m0 .. m0 + U - 1 of a slice for this lane (slot and value; 0 past the lane's
+// list). off is the first entry of step m0 and is advanced past the batch: step m holds one
+// entry for every lane whose list is longer than m, and those lanes come first.
+template <typename V, int U>
+__device__ __forceinline__ void owner_load_batch(const uint16_t* __restrict__ S, const V* __restrict__ Vv, int m0,
+                                                 int len, int lane, int64_t& off, uint32_t (&sv)[U], V (&vv)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const bool act = m0 + u < len;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    sv[u] = 0u;
+    vv[u] = V(0);
+    if (act) {
+      sv[u] = owner_ld(S + off + lane);
+      vv[u] = owner_ldv(Vv + off + lane);
+    }
+    off += __popc(bal);
+  }
+}
+
+// The multiply-adds of steps m0 .. m0 + U - 1 of this lane: x of each entry's slot from the
+// window, one multiply-add per column.
+template <typename A, typename V, int U, int RK>
+__device__ __forceinline__ void owner_fma_batch(const A* xs, int m0, int len, const uint32_t (&sv)[U],
+                                                const V (&vv)[U], A (&acc)[RK]) {
+  A xv[U][RK];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int c = 0; c < RK; ++c) xv[u][c] = xs[sv[u] * RK + c];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (m0 + u < len) {
+      const A v = owner_widen(vv[u]);
+#pragma unroll
+      for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[u][c], acc[c]);
+    }
+  }
+}
+
+// Loads of the U steps of batch bi of a slice's regular part (every lane active): entry
+// (m, lane) is at pS[32 m] / pV[32 m], pS and pV pointing at the lane's entry of step 0.
+template <typename V, int U>
+__device__ __forceinline__ void owner_load_full(const uint16_t* __restrict__ pS, const V* __restrict__ pV, int bi,
+                                                uint32_t (&sv)[U], V (&vv)[U]) {
+  const int m0 = bi * U;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    sv[u] = owner_ld(pS + (size_t)kOwnerLanes * (m0 + u));
+    vv[u] = owner_ldv(pV + (size_t)kOwnerLanes * (m0 + u));
+  }
+}
+
+// The multiply-adds of a full batch (every step active for this lane).
+template <typename A, typename V, int U, int RK>
+__device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)[U], const V (&vv)[U],
+                                               A (&acc)[RK]) {
+  A xv[U][RK];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int c = 0; c < RK; ++c) xv[u][c] = xs[sv[u] * RK + c];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const A v = owner_widen(vv[u]);
+#pragma unroll
+    for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[u][c], acc[c]);
+  }
+}
+
+// Steps per batch of loads (two batches are in flight per warp): deeper for 4- and 2-byte
+// values, whose multiply-adds are too quick to hide a batch's latency on their own.
+template <int ST>
+constexpr int owner_unroll(int rk) {
+  return rk == 1 ? 4 : (rk == 2 ? 4 : 2);
+}
 
 // Band b of the product described by a, run by the whole CTA.
 template <int ST, int RK>
@@ -69,7 +143,7 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
   using V = typename OwnerTypes<ST>::V;
   using X = typename OwnerTypes<ST>::X;
   using A = typename OwnerTypes<ST>::A;
-  constexpr int U = owner_unroll(RK);
+  constexpr int U = owner_unroll<ST>(RK);
   extern __shared__ __align__(16) unsigned char owner_smem[];
   A* xs = reinterpret_cast<A*>(owner_smem);  // window: x of slot s, column c at s * RK + c
   const int4 bd = __ldg(a.band + b);
@@ -79,14 +153,29 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
   const int tid = threadIdx.x;
   const int T = blockDim.x;
 
-  // ---- the window's x: spill rows (gathered through their row list), then own rows
-  for (int i = tid; i < nsp * RK; i += T) {
-    const int s = i / RK, c = i % RK;
-    xs[i] = (A)__ldg(x + (size_t)__ldg(a.spill_row + sbase + s) * ldx + c);
-  }
-  for (int i = tid; i < nown * RK; i += T) {
-    const int s = i / RK, c = i % RK;
-    xs[nsp * RK + i] = (A)__ldg(x + (size_t)(r0 + s) * ldx + c);
+  // ---- the window's x: spill rows (gathered through their row list), then own rows; each
+  // thread issues kWin loads before it stores any, so that their latencies overlap
+  constexpr int kWin = 8;
+  const int nsx = nsp * RK, nox = nown * RK;
+  for (int i0 = tid; i0 < nsx + nox; i0 += kWin * T) {
+    A v[kWin];
+    int row[kWin];
+#pragma unroll
+    for (int u = 0; u < kWin; ++u) {
+      const int i = i0 + u * T;
+      row[u] = i < nsx ? __ldg(a.spill_row + sbase + i / RK) : r0 + (i - nsx) / RK;
+    }
+#pragma unroll
+    for (int u = 0; u < kWin; ++u) {
+      const int i = i0 + u * T;
+      const int c = (i < nsx ? i : i - nsx) % RK;
+      v[u] = i < nsx + nox ? (A)__ldg(x + (size_t)row[u] * ldx + c) : A(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kWin; ++u) {
+      const int i = i0 + u * T;
+      if (i < nsx + nox) xs[i] = v[u];
+    }
   }
   __syncthreads();
 
@@ -101,42 +190,45 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
     const uint32_t w = __ldg(a.lane + (size_t)q * kOwnerLanes + lane);
     const int len = (int)(w >> 16);
     const int slot = (int)(w & 0xffffu);
-    const int maxlen = __shfl_sync(0xffffffffu, len, 0);  // lengths descend across the slice
-    int64_t off = __ldg(a.slice_off + q);                  // first entry of the current step
+    // lengths descend across the slice: lane 0 has the longest list, lane 31 the shortest
+    const int maxlen = __shfl_sync(0xffffffffu, len, 0);
+    const int minlen = __shfl_sync(0xffffffffu, len, 31);
+    const int64_t base = __ldg(a.slice_off + q);
     A acc[RK];
 #pragma unroll
     for (int c = 0; c < RK; ++c) acc[c] = A(0);
-    for (int m0 = 0; m0 < maxlen; m0 += U) {
+    // Regular part: steps m < minlen hold all 32 lanes, entry (m, lane) at base + 32 m + lane,
+    // so each lane walks one pointer with fixed offsets. Two batches of U steps are in flight
+    // in a ring of registers: a batch's loads are issued two compute phases before its
+    // multiply-adds, so that memory latency overlaps this and other warps' arithmetic.
+    const uint16_t* __restrict__ pS = S + base + lane;
+    const V* __restrict__ pV = Vv + base + lane;
+    const int nfull = minlen / U;  // batches of U steps with every lane active
+    {
+      uint32_t s0[U], s1[U];
+      V v0[U], v1[U];
+      if (nfull > 0) owner_load_full<V, U>(pS, pV, 0, s0, v0);
+      if (nfull > 1) owner_load_full<V, U>(pS, pV, 1, s1, v1);
+      int bi = 0;
+      for (; bi + 1 < nfull; bi += 2) {
+        owner_fma_full<A, V, U, RK>(xs, s0, v0, acc);
+        if (bi + 2 < nfull) owner_load_full<V, U>(pS, pV, bi + 2, s0, v0);
+        owner_fma_full<A, V, U, RK>(xs, s1, v1, acc);
+        if (bi + 3 < nfull) owner_load_full<V, U>(pS, pV, bi + 3, s1, v1);
+      }
+      if (bi < nfull) owner_fma_full<A, V, U, RK>(xs, s0, v0, acc);
+    }
+    // Ragged tail: steps m >= nfull * U, where lanes whose list has ended drop out; step m
+    // holds one entry for each lane whose list is longer than m (those lanes come first).
+    int64_t off = base + (int64_t)kOwnerLanes * nfull * U;
+    for (int m0 = nfull * U; m0 < maxlen; m0 += U) {
       uint32_t sv[U];
       V vv[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool act = m0 + u < len;
-        const unsigned bal = __ballot_sync(0xffffffffu, act);
-        sv[u] = 0u;
-        vv[u] = V(0);
-        if (act) {
-          sv[u] = owner_ld(S + off + lane);
-          vv[u] = owner_ldv(Vv + off + lane);
-        }
-        off += __popc(bal);
-      }
-      A xv[U][RK];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int c = 0; c < RK; ++c) xv[u][c] = xs[sv[u] * RK + c];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (m0 + u < len) {
-          const A v = owner_widen(vv[u]);
-#pragma unroll
-          for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[u][c], acc[c]);
-        }
-      }
+      owner_load_batch<V, U>(S, Vv, m0, len, lane, off, sv, vv);
+      owner_fma_batch<A, V, U, RK>(xs, m0, len, sv, vv, acc);
     }
     if (slot < nsp) {
-      A* sp = static_cast<A*>(a.spill) + (size_t)(sbase + slot) * RK;
+      A* sp = static_cast<A*>(a.spill) + (size_t)__ldg(a.spill_pos + sbase + slot) * RK;
 #pragma unroll
       for (int c = 0; c < RK; ++c) sp[c] = acc[c];
     } else if (slot != (int)kOwnerPadSlot) {

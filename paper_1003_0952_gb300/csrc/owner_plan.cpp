@@ -209,8 +209,8 @@ void run_workers(int workers, F&& fn) {
 }  // namespace
 
 void free_owner_plan(OwnerPlan& p) {
-  void* ptrs[] = {p.band, p.band_slice, p.slice_off, p.lane, p.spill_row, p.S, p.VA,
-                  p.VT == p.VA ? nullptr : p.VT, p.acc_row, p.acc_ptr, p.acc_src, p.spill_buf};
+  void* ptrs[] = {p.band, p.band_slice, p.slice_off, p.lane, p.spill_row, p.spill_pos, p.S, p.VA,
+                  p.VT == p.VA ? nullptr : p.VT, p.acc_row, p.acc_ptr, p.spill_buf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p = OwnerPlan();
@@ -296,8 +296,8 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
     }
   std::vector<int32_t> first((size_t)n + 1, 0);
   for (int32_t r = 0; r < n; ++r) first[(size_t)r + 1] = first[(size_t)r] + cnt[(size_t)r + 1];
-  std::vector<int32_t> acc_src((size_t)std::max<int64_t>(1, spill));
-  for (int64_t g = 0; g < spill; ++g) acc_src[(size_t)first[(size_t)spill_row[(size_t)g]]++] = (int32_t)g;
+  std::vector<int32_t> spill_pos((size_t)std::max<int64_t>(1, spill));
+  for (int64_t g = 0; g < spill; ++g) spill_pos[(size_t)g] = first[(size_t)spill_row[(size_t)g]]++;
   // ---- upload
   OwnerPlan p;
   p.nb = nb;
@@ -324,7 +324,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   up(&p.S, S);
   up(&p.acc_row, acc_row);
   up(&p.acc_ptr, acc_ptr);
-  up(&p.acc_src, acc_src);
+  up(&p.spill_pos, spill_pos);
   if (e == cudaSuccess)
     e = cudaMalloc(&p.spill_buf, std::max<size_t>(1, (size_t)spill * (size_t)rk * (size_t)spill_bytes));
   int64_t* dcode = nullptr;
