@@ -26,6 +26,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,7 +42,7 @@ if ROOT not in sys.path:
 
 METRIC = "CSRC SpMV GB/s and % of HBM roofline (FP64 vs mixed-prec batched, 1 GB300)"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["kernels.cu", "band.cuh", "df32.cuh", "internal.h"]
+KERNEL_SOURCES = ["owner.cuh", "owner.cu", "internal.h"]
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -195,7 +196,7 @@ def describe(name: str, m) -> dict:
 def oracle_gbs(m, x, budget_s: float, max_rows: int | None = None):
     """Time the oracle's Fig. 2(a) product (and its transpose) on the leading
     max_rows x max_rows principal submatrix, repeating until budget_s passes.
-    Returns (GB/s, products, seconds, rows)."""
+    Returns (GB/s, products, seconds, rows, y, y_t): the last A x and A^T x."""
     import oracle
 
     c = oracle.from_matrix(m)
@@ -207,13 +208,13 @@ def oracle_gbs(m, x, budget_s: float, max_rows: int | None = None):
     nbytes = model_bytes(rows, c.pairs)
     done, t0 = 0, time.perf_counter()
     while True:
-        oracle.csrc_spmv(c, xs)
-        oracle.csrc_spmv_t(c, xs)
+        y = oracle.csrc_spmv(c, xs)
+        yt = oracle.csrc_spmv_t(c, xs)
         done += 2
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return nbytes * done / el / 1e9, done, el, rows
+    return nbytes * done / el / 1e9, done, el, rows, y, yt
 
 
 def run_reference(args):
@@ -224,7 +225,7 @@ def run_reference(args):
     # calibrate: one product pair on a sample, then size each step to fit the budget
     total_budget = 120.0
     per_step = total_budget / max(1, args.steps + args.warmup)
-    _, _, el, rows = oracle_gbs(m, x, 0.0, max_rows=min(m.n, 200_000))
+    _, _, el, rows, _, _ = oracle_gbs(m, x, 0.0, max_rows=min(m.n, 200_000))
     rows_step = int(max(1000, min(m.n, rows * per_step / max(el, 1e-6))))
     import oracle
 
@@ -333,6 +334,9 @@ def run_ours(args):
             step_host()
         e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
         barrier(world)
+        # the results of the last timed step, for the check against the oracle
+        y_last = y.double().cpu().numpy()
+        yt_last = yt.double().cpu().numpy()
         st = cs.csrc_get_last_device_error(h)
         if st != cs.CSRC_OK:
             raise RuntimeError(f"device status after the timed steps: {cs.csrc_status_string(st)}")
@@ -344,17 +348,23 @@ def run_ours(args):
     e2e_value = replica_throughput(world, nbytes_step, args.steps, e2e_s)
     peak, peak_src = measured_hbm()
     nprod, ms_prod = ktimes["product"]
-    # algorithmic bytes of one band-kernel launch: the CSRC working set plus its spill writes
+    # algorithmic bytes of one product-kernel launch: the CSRC working set (Table 1's ws) plus
+    # the spill writes of the bands (SURVEY.md's accumulation traffic counted explicitly)
     vec_bytes = 8 if args.storage == "f64" else 4
     kbytes = int(info["model_bytes"]) + vec_bytes * int(info["spill_entries"])
-    achieved = kbytes / (ms_prod / max(nprod, 1) * 1e-3) / 1e9 if nprod else None
+    launch_ms = ms_prod / max(nprod, 1)
+    achieved = kbytes / (launch_ms * 1e-3) / 1e9 if nprod else None
     launches = sum(v[0] for v in ktimes.values())
     if rank != 0:
         return 0
     cfg = describe(args.workload, m)
-    cfg.update({"nbands": info["nbands"], "spill_entries": info["spill_entries"],
-                "arith": {0: "double-float (FP32 pairs)", 1: "FP64 pipe", 2: "FP32"}[info["arith"]],
+    window = args.strategy in ("window", "auto") and info["tuned_strategy"] in (0, 1)
+    arith = ("FP64 pipe: one FP64 multiply-add per stored value" if args.storage == "f64" and
+             (window or info["arith"] == 1) else {0: "double-float (FP32 pairs)", 1: "FP64 pipe", 2: "FP32"}[info["arith"]])
+    cfg.update({"nbands": info["nbands"], "spill_entries": info["spill_entries"], "arith": arith,
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
+    kname = ("owner_kernel (window strategy: target-sorted entry lists, one lane per window row)" if window
+             else "band_kernel (stream-order strategy)")
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -365,20 +375,30 @@ def run_ours(args):
         "pct_hbm_roofline": value / world / peak,
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": 2 * xh.element_size() * m.n,
                 "d2h_bytes_per_step": 2 * xh.element_size() * m.n},
-        "roofline": {"bound": "hbm", "kernel": "band_kernel (product)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "peak_source": f"{peak_src} hbm_gbs", "traffic": ncu_traffic(args.workload),
-                     "algorithmic_bytes_per_launch": kbytes,
-                     "launch_ms": ms_prod / max(nprod, 1)},
+                     "peak_source": f"{peak_src} hbm_gbs", "traffic": ncu_traffic(args.workload) if window else None,
+                     "algorithmic_bytes_per_launch": kbytes, "launch_ms": launch_ms,
+                     # what the window strategy's kernel itself moves (entry slots and values, list
+                     # metadata, x of every window slot, y and spill writes), for comparison
+                     "kernel_bytes_per_launch": int(info["list_bytes"]) if window else None},
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in ktimes.items()},
         "gpu_launches": launches,
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
-        gbs, done, el, rows = oracle_gbs(m, x_np, args.cpu_seconds)
+        import oracle
+
+        xs64 = x.double().cpu().numpy() if args.storage != "f64" else x_np
+        gbs, done, el, rows, yref, ytref = oracle_gbs(m, xs64, args.cpu_seconds)
+        tol = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}[args.storage]
+        err = {"A x": oracle.max_rel_err(m, xs64, y_last, yref),
+               "A^T x": oracle.max_rel_err(m, xs64, yt_last, ytref, transpose=True)}
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{done} full products (y = A x and y = A^T x alternating) of the "
                                           f"workload in {el:.1f} s, single-threaded FP64 C"}
+        # the same oracle products check the timed steps' results: max_i |y_i - yref_i| / sum_j |a_ij||x_j|
+        line["max_rel_err"] = {**err, "tolerance": tol, "ok": all(v <= tol for v in err.values())}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -388,29 +408,49 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------------------- suite of every configuration
-def _events_ms(fn, iters: int) -> float:
+def _events_ms(fn, iters: int, runs: int = 3) -> float:
+    """Median over `runs` runs of the mean device time of `iters` back-to-back calls of fn
+    (CUDA events on the current stream, after three warm-up calls)."""
     import torch
 
     for _ in range(3):
         fn()
     torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(iters):
-        fn()
-    b.record()
-    torch.cuda.synchronize()
-    return a.elapsed_time(b) / iters
+    times = []
+    for _ in range(runs):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(iters):
+            fn()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b) / iters)
+    return statistics.median(times)
+
+
+def _oracle_leg(fn, nbytes: int):
+    """CPU baseline of one suite row: the oracle's products timed once on the host (one
+    core), returned with their results so that the row's GPU results can be checked."""
+    t0 = time.perf_counter()
+    out = fn()
+    el = time.perf_counter() - t0
+    return out, {"value": nbytes / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle", "seconds": el}
+
+
+SUITE_TOL = {"f64": 1e-12, "f32": 1e-5, "bf16": 1e-2}
 
 
 def run_suite(args):
-    """One JSON line per configuration row: FP64 strategies, FP32 / BF16 storage, several
-    right-hand sides and the batched graph launch. Device time with CUDA events; every
-    row's inputs are larger than L2 except the P1 100x100 one (marked)."""
+    """One JSON line per configuration row of the contract (C1-C5) and of the next steps
+    (N1-N4). Device time: median of three runs of --suite-iters calls, CUDA events on the
+    launch stream. Every row carries a CPU baseline (the oracle timed on the host) and the
+    max relative error of the row's GPU results against those oracle results. Inputs are
+    larger than L2 except C1's, which is timed both L2-resident and over rotating copies."""
     import torch
 
     import fe_inputs as fe
+    import oracle
     import paper_1003_0952_gb300 as cs
 
     torch.cuda.set_device(0)
@@ -422,51 +462,100 @@ def run_suite(args):
         d["frac_of_measured_hbm"] = d["GB/s"] / peak if "GB/s" in d else None
         print(json.dumps(d), flush=True)
 
+    def gpu(t):
+        return t.double().cpu().numpy()
+
     def spmv_rows(name, m, storages, strategies, colour=False):
         xs = fe.source_vector(m.n, 7)
+        c = oracle.from_matrix(m)
         for storage in storages:
             vb = {"f64": 8, "f32": 4, "bf16": 2}[storage]
             xb = 8 if storage == "f64" else 4
+            x64 = xs if storage == "f64" else xs.astype(np.float32).astype(np.float64)
+            mb = model_bytes(m.n, m.pairs, vb, xb)
+            (yref, ytref), cpu = _oracle_leg(lambda: (oracle.csrc_spmv(c, x64), oracle.csrc_spmv_t(c, x64)),
+                                             2 * model_bytes(m.n, m.pairs))
             h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
             try:
                 cs.csrc_partition(h, 0)
                 if colour:
                     cs.csrc_color(h, 12345)
                 dt = torch.float64 if storage == "f64" else torch.float32
-                x = torch.from_numpy(xs).to(dt).cuda()
+                x = torch.from_numpy(x64).to(dt).cuda()
                 y = torch.empty_like(x)
-                mb = model_bytes(m.n, m.pairs, vb, xb)
+                yt = torch.empty_like(x)
                 for strat in strategies:
                     if strat == "color" and not colour:
                         continue
                     code = cs.STRATEGIES[strat]
-                    ms = _events_ms(lambda: (cs.csrc_spmv(h, x, y, code, sptr), cs.csrc_spmv_t(h, x, y, code, sptr)),
+                    ms = _events_ms(lambda: (cs.csrc_spmv(h, x, y, code, sptr), cs.csrc_spmv_t(h, x, yt, code, sptr)),
                                     args.suite_iters) / 2
+                    err = max(oracle.max_rel_err(m, x64, gpu(y), yref),
+                              oracle.max_rel_err(m, x64, gpu(yt), ytref, transpose=True))
                     info = cs.csrc_get_info(h)
                     emit({"suite": name, "n": m.n, "nnz": m.nnz, "storage": storage, "strategy": strat,
                           "ms_per_product": ms, "GB/s": mb / ms / 1e6, "GFLOP/s": flops(m.n, m.pairs) / ms / 1e6,
-                          "nbands": info["nbands"], "spill_entries": info["spill_entries"],
-                          "ncolors": info["ncolors"], "lanes_per_row": info["group"]})
+                          "model_bytes": mb, "nbands": info["nbands"] if strat == "window" else info["stream_nbands"],
+                          "spill_entries": info["spill_entries"] if strat == "window" else info["stream_spill_entries"],
+                          "ncolors": info["ncolors"], "max_rel_err": err, "tolerance": SUITE_TOL[storage],
+                          "cpu_baseline": cpu})
                 if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
                     raise RuntimeError("device status")
             finally:
                 cs.csrc_destroy(h)
 
+    def rotating_rows(name, m, copies):
+        # the matrix fits in L2: time the window product over `copies` handles of it in turn,
+        # so that each product reads its matrix from HBM (the copies together exceed L2 four times)
+        xs = fe.source_vector(m.n, 7)
+        c = oracle.from_matrix(m)
+        (yref, ytref), cpu = _oracle_leg(lambda: (oracle.csrc_spmv(c, xs), oracle.csrc_spmv_t(c, xs)),
+                                         2 * model_bytes(m.n, m.pairs))
+        hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64) for _ in range(copies)]
+        try:
+            for h in hs:
+                cs.csrc_partition(h, 0)
+            xd = [torch.from_numpy(xs).cuda() for _ in range(copies)]
+            yd = [torch.empty_like(v) for v in xd]
+
+            def run():
+                for h, v, w in zip(hs, xd, yd):
+                    cs.csrc_spmv(h, v, w, cs.CSRC_STRAT_WINDOW, sptr)
+
+            ms = _events_ms(run, max(1, args.suite_iters // 10)) / copies
+            err = oracle.max_rel_err(m, xs, gpu(yd[-1]), yref)
+            cs.csrc_spmv_t(hs[0], xd[0], yd[0], cs.CSRC_STRAT_WINDOW, sptr)
+            err = max(err, oracle.max_rel_err(m, xs, gpu(yd[0]), ytref, transpose=True))
+            mb = model_bytes(m.n, m.pairs)
+            emit({"suite": name, "n": m.n, "nnz": m.nnz, "storage": "f64", "strategy": "window",
+                  "copies": copies, "ms_per_product": ms, "GB/s": mb / ms / 1e6,
+                  "GFLOP/s": flops(m.n, m.pairs) / ms / 1e6, "max_rel_err": err, "tolerance": 1e-12,
+                  "cpu_baseline": cpu})
+        finally:
+            for h in hs:
+                cs.csrc_destroy(h)
+
+    strategies = ["window", "window_atomic", "atomic", "color"]
     sel = set(args.suite.split(",")) if args.suite != "all" else {"c1", "c2", "c3", "c4", "c5", "n1", "n2", "n3", "n4"}
     if "c1" in sel:
         m, _ = build_workload("p1_100x100")
-        spmv_rows("C1 p1_100x100 (fits in L2)", m, ["f64"], ["window", "atomic", "color"], colour=True)
+        spmv_rows("C1 p1_100x100 (fits in L2: L2-resident figure)", m, ["f64"], strategies, colour=True)
+        rotating_rows("C1 p1_100x100 over rotating copies (HBM-resident figure)", m,
+                      int(math.ceil(4 * 129e6 / model_bytes(m.n, m.pairs))))
     if "c2" in sel:
         for wl in ("q1s_96", "q1v_96"):
             m, _ = build_workload(wl)
-            spmv_rows(f"C2 {wl}", m, ["f64"], ["window", "atomic", "color"], colour=True)
+            spmv_rows(f"C2 {wl}", m, ["f64", "f32", "bf16"] if wl == "q1v_96" else ["f64"], strategies,
+                      colour=True)
             del m
     if "c3" in sel:
         m = fe.tet_mesh(2_000_000, 1003, method=args.tet_method)
-        spmv_rows(f"C3 tet_{args.tet_method}_2m", m, ["f64", "f32"], ["window"])
+        spmv_rows(f"C3 tet_{args.tet_method}_2m", m, ["f64", "f32", "bf16"], ["window", "window_atomic"])
         del m
+
     if "c4" in sel:
         m, _ = build_workload("q1s_96")
+        c = oracle.from_matrix(m)
         for storage in ("f64", "bf16"):
             vb = {"f64": 8, "bf16": 2}[storage]
             xb = 8 if storage == "f64" else 4
@@ -474,34 +563,45 @@ def run_suite(args):
             try:
                 cs.csrc_partition(h, 0)
                 dt = torch.float64 if storage == "f64" else torch.float32
+                x1 = torch.from_numpy(fe.source_vector(m.n, 8)).to(dt).cuda()
+                y1 = torch.empty_like(x1)
+                ms1 = _events_ms(lambda: cs.csrc_spmv(h, x1, y1, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
                 for r in (4, 8, 16, 32):
-                    X = torch.from_numpy(fe.source_vector(m.n, 8, nrhs=r)).to(dt).cuda()
+                    Xn = fe.source_vector(m.n, 8, nrhs=r)
+                    if storage != "f64":
+                        Xn = Xn.astype(np.float32).astype(np.float64)
+                    X = torch.from_numpy(Xn).to(dt).cuda()
                     Y = torch.empty_like(X)
                     cs.csrc_autotune_spmm(h, X, Y, r, sptr)
                     rk = cs.csrc_get_info(h)["tuned_rk"]
                     ms = _events_ms(lambda: cs.csrc_spmm_batched([h], [X], [Y], r, False, sptr), args.suite_iters)
+                    Yref, cpu = _oracle_leg(lambda: oracle.csrc_spmm(c, Xn), r * model_bytes(m.n, m.pairs))
+                    err = oracle.max_rel_err(m, Xn, gpu(Y), Yref)
                     matrix = 4 * (m.n + 1) + 4 * m.pairs + 2 * vb * m.pairs + vb * m.n
                     mb = matrix + 2 * r * m.n * xb
                     passes = (r + rk - 1) // rk if rk else 1
                     emit({"suite": "C4 q1s_96 several right-hand sides", "storage": storage, "nrhs": r,
                           "k_tile": rk, "ms": ms, "GB/s": mb / ms / 1e6,
                           "GFLOP/s": r * flops(m.n, m.pairs) / ms / 1e6,
-                          "streamed_GB/s": (passes * matrix + 2 * r * m.n * xb) / ms / 1e6})
+                          "streamed_GB/s": (passes * matrix + 2 * r * m.n * xb) / ms / 1e6,
+                          "single_vector_ms": ms1, "speedup_vs_r_single_products": r * ms1 / ms,
+                          "max_rel_err": err, "tolerance": SUITE_TOL[storage], "cpu_baseline": cpu})
                     del X, Y
             finally:
                 cs.csrc_destroy(h)
-        del m
+        del m, c
     if "n1" in sel:
         # rectangular CSRC (Section 2.1): the first half of q1v_96's rows as one subdomain of an
         # overlapping decomposition, its overlap columns in the auxiliary CSR
         g, _ = build_workload("q1v_96")
         a = fe.overlap_subdomain(g, g.n // 2, "q1v_96_half")
         del g
+        r = oracle.csr_to_csrcr(a.n, a.m, a.row_ptr, a.col, a.val)
         h = cs.csrc_create_rect_from_csr(a.n, a.m, a.row_ptr, a.col, a.val, cs.CSRC_F64)
         try:
             cs.csrc_partition(h, 0)
-            xm = torch.from_numpy(fe.source_vector(a.m, 10)).cuda()
-            xn = torch.from_numpy(fe.source_vector(a.n, 11)).cuda()
+            xmn, xnn = fe.source_vector(a.m, 10), fe.source_vector(a.n, 11)
+            xm, xn = torch.from_numpy(xmn).cuda(), torch.from_numpy(xnn).cuda()
             yn = torch.empty(a.n, dtype=torch.float64, device="cuda")
             ym = torch.empty(a.m, dtype=torch.float64, device="cuda")
             info = cs.csrc_get_info(h)
@@ -509,66 +609,89 @@ def run_suite(args):
             for tr in (False, True):
                 if tr:
                     ms = _events_ms(lambda: cs.csrc_spmv_t(h, xn, ym, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+                    ref, cpu = _oracle_leg(lambda: oracle.csrcr_spmv_t(r, xnn), mb)
+                    err = oracle.max_rel_err_rect(a.n, a.m, a.row_ptr, a.col, a.val, xnn, gpu(ym), ref, transpose=True)
                 else:
                     ms = _events_ms(lambda: cs.csrc_spmv(h, xm, yn, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
+                    ref, cpu = _oracle_leg(lambda: oracle.csrcr_spmv(r, xmn), mb)
+                    err = oracle.max_rel_err_rect(a.n, a.m, a.row_ptr, a.col, a.val, xmn, gpu(yn), ref)
                 emit({"suite": "N1 rectangular CSRC: q1v_96 half-domain with overlap", "n": a.n, "m": a.m,
                       "aux_nnz": info["rect_nnz"], "storage": "f64", "strategy": "window",
-                      "product": "A^T x" if tr else "A x", "ms_per_product": ms, "GB/s": mb / ms / 1e6})
+                      "product": "A^T x" if tr else "A x", "ms_per_product": ms, "GB/s": mb / ms / 1e6,
+                      "max_rel_err": err, "tolerance": 1e-12, "cpu_baseline": cpu})
             if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
                 raise RuntimeError("device status")
         finally:
             cs.csrc_destroy(h)
-        del a
+        del a, r
     if "n2" in sel:
         # numerically symmetric storage (Section 2.2): q1v_96's pattern with a_ji = a_ij, au not stored
         g, _ = build_workload("q1v_96")
         rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
         g.val = fe.hash_uniform(1006, np.minimum(rows, g.col), np.maximum(rows, g.col))
         del rows
+        c = oracle.from_matrix(g)
+        xn = fe.source_vector(g.n, 12)
         h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.CSRC_F64, cs.CSRC_FLAG_SYMMETRIC_VALUES)
         try:
             cs.csrc_partition(h, 0)
-            x = torch.from_numpy(fe.source_vector(g.n, 12)).cuda()
+            x = torch.from_numpy(xn).cuda()
             y = torch.empty_like(x)
             mb = cs.csrc_get_info(h)["model_bytes"]  # 6 nnz + 22 n + 4
-            ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
-            emit({"suite": "N2 numerically symmetric CSRC (au not stored): q1v_96 pattern", "n": g.n, "nnz": g.nnz,
-                  "storage": "f64", "strategy": "window", "ms_per_product": ms, "model_bytes": mb,
-                  "GB/s": mb / ms / 1e6, "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6})
+            ref, cpu = _oracle_leg(lambda: oracle.csrc_spmv(c, xn), model_bytes(g.n, g.pairs))
+            for strat in ("window", "window_atomic"):
+                code = cs.STRATEGIES[strat]
+                ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, code, sptr), args.suite_iters)
+                emit({"suite": "N2 numerically symmetric CSRC (au not stored): q1v_96 pattern", "n": g.n,
+                      "nnz": g.nnz, "storage": "f64", "strategy": strat, "ms_per_product": ms, "model_bytes": mb,
+                      "GB/s": mb / ms / 1e6, "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6,
+                      "max_rel_err": oracle.max_rel_err(g, xn, gpu(y), ref), "tolerance": 1e-12,
+                      "cpu_baseline": cpu})
             if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
                 raise RuntimeError("device status")
         finally:
             cs.csrc_destroy(h)
-        del g
+        del g, c
     if "n3" in sel:
-        # index compression: 16-bit band-local window slots instead of 32-bit ones, q1v_96
+        # index compression: 16-bit band-local window slots instead of 32-bit ones, q1v_96. The
+        # window strategy's lists always use 16-bit slots; the stream-order kernel has both forms.
         g, _ = build_workload("q1v_96")
+        c = oracle.from_matrix(g)
         xs = fe.source_vector(g.n, 13)
         for storage in ("f64", "bf16"):
-            for flags, label in ((0, "32-bit slots"), (cs.CSRC_FLAG_COMPRESS_INDICES, "16-bit slots")):
+            x64 = xs if storage == "f64" else xs.astype(np.float32).astype(np.float64)
+            ref, cpu = _oracle_leg(lambda: oracle.csrc_spmv(c, x64), model_bytes(g.n, g.pairs))
+            for flags, label, strat in ((0, "16-bit slots (entry lists)", "window"),
+                                        (0, "32-bit slots", "window_atomic"),
+                                        (cs.CSRC_FLAG_COMPRESS_INDICES, "16-bit slots", "window_atomic")):
                 h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.STORAGE[storage], flags)
                 try:
                     cs.csrc_partition(h, 0)
                     dt = torch.float64 if storage == "f64" else torch.float32
-                    x = torch.from_numpy(xs).to(dt).cuda()
+                    x = torch.from_numpy(x64).to(dt).cuda()
                     y = torch.empty_like(x)
-                    mb = cs.csrc_get_info(h)["model_bytes"]
-                    ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr), args.suite_iters)
-                    emit({"suite": "N3 index compression: q1v_96", "storage": storage, "indices": label,
-                          "ms_per_product": ms, "model_bytes": mb, "GB/s": mb / ms / 1e6,
-                          "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6})
+                    code = cs.STRATEGIES[strat]
+                    ms = _events_ms(lambda: cs.csrc_spmv(h, x, y, code, sptr), args.suite_iters)
+                    info = cs.csrc_get_info(h)
+                    mb = info["model_bytes"] if strat != "window" else info["model_bytes"] - 2 * g.pairs
+                    emit({"suite": "N3 index compression: q1v_96", "storage": storage, "strategy": strat,
+                          "indices": label, "ms_per_product": ms, "model_bytes": mb, "GB/s": mb / ms / 1e6,
+                          "GFLOP/s": flops(g.n, g.pairs) / ms / 1e6,
+                          "max_rel_err": oracle.max_rel_err(g, x64, gpu(y), ref), "tolerance": SUITE_TOL[storage],
+                          "cpu_baseline": cpu})
                     if cs.csrc_get_last_device_error(h) != cs.CSRC_OK:
                         raise RuntimeError("device status")
                 finally:
                     cs.csrc_destroy(h)
-        del g
+        del g, c
     if "n4" in sel:
         # BiCG (csrc_bicg) on q1v_96: one A p and one A^T p* per iteration plus two vector passes
         g, _ = build_workload("q1v_96")
+        bn = fe.source_vector(g.n, 14)
         h = cs.csrc_create_from_csr(g.n, g.row_ptr, g.col, g.val, cs.CSRC_F64)
         try:
             cs.csrc_partition(h, 0)
-            b = torch.from_numpy(fe.source_vector(g.n, 14)).cuda()
+            b = torch.from_numpy(bn).cuda()
             x = torch.zeros_like(b)
             cs.csrc_bicg(h, b, x, 1e-8, 3)  # warm-up (plans, scratch)
             x.zero_()
@@ -578,11 +701,15 @@ def run_suite(args):
             torch.cuda.synchronize()
             ms = (time.perf_counter() - t0) * 1e3
             it = max(res["iters"], 1)
+            # true residual of the GPU solution, through the oracle's CSR product
+            r_true, cpu = _oracle_leg(lambda: bn - oracle.csr_spmv(g.n, g.row_ptr, g.col, g.val, gpu(x)),
+                                      model_bytes(g.n, g.pairs))
             # per iteration: two products (model bytes each) and 19 n vector reads/writes of 8 bytes
             per_it = 2 * cs.csrc_get_info(h)["model_bytes"] + 19 * 8 * g.n
             emit({"suite": "N4 BiCG on q1v_96 (csrc_bicg, FP64, window)", "status": res["status"],
-                  "iters": res["iters"], "relres": res["relres"], "ms_total_host_clock": ms,
-                  "ms_per_iteration": ms / it, "GB/s": per_it * it / ms / 1e6})
+                  "iters": res["iters"], "relres": res["relres"],
+                  "true_relres": float(np.linalg.norm(r_true) / np.linalg.norm(bn)), "ms_total_host_clock": ms,
+                  "ms_per_iteration": ms / it, "GB/s": per_it * it / ms / 1e6, "cpu_baseline": cpu})
         finally:
             cs.csrc_destroy(h)
         del g
@@ -590,18 +717,22 @@ def run_suite(args):
         ms_list = fe.batch_meshes(256, 1005)
         tot_n = sum(m.n for m in ms_list)
         tot_pairs = sum(m.pairs for m in ms_list)
+        xs = [fe.source_vector(m.n, 9 + i) for i, m in enumerate(ms_list)]
+        cs_list = [oracle.from_matrix(m) for m in ms_list]
+        refs, cpu = _oracle_leg(lambda: [oracle.csrc_spmv(c, x) for c, x in zip(cs_list, xs)],
+                                sum(model_bytes(m.n, m.pairs) for m in ms_list))
         res = {}
         for storage in ("f32", "f64"):
             hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage]) for m in ms_list]
             try:
                 dt = torch.float64 if storage == "f64" else torch.float32
-                X = [torch.from_numpy(fe.source_vector(m.n, 9 + i)).to(dt).cuda() for i, m in enumerate(ms_list)]
+                X = [torch.from_numpy(x).to(dt).cuda() for x in xs]
                 Y = [torch.empty_like(x) for x in X]
                 if storage == "f32":
                     for h, x, y in zip(hs, X, Y):
                         cs.csrc_autotune(h, x, y, sptr)
                     ms = _events_ms(lambda: cs.csrc_spmm_batched(hs, X, Y, 1, False, sptr), args.suite_iters)
-                    vb, xb, how = 4, 4, "one CUDA-graph replay: persistent band kernels over all 256 members"
+                    vb, xb, how = 4, 4, "one CUDA-graph replay over all 256 members"
                 else:
                     for h in hs:
                         cs.csrc_partition(h, 0)
@@ -611,12 +742,17 @@ def run_suite(args):
                             cs.csrc_spmv(h, x, y, cs.CSRC_STRAT_WINDOW, sptr)
 
                     ms = _events_ms(separate, max(3, args.suite_iters // 4))
-                    vb, xb, how = 8, 8, "256 separate csrc_spmv calls (band + accumulation launches each)"
+                    vb, xb, how = 8, 8, "256 separate csrc_spmv calls (product + accumulation launches each)"
+                torch.cuda.synchronize()
+                err = max(oracle.max_rel_err(m, x if storage == "f64" else x.astype(np.float32).astype(np.float64),
+                                             gpu(y), ref)
+                          for m, x, y, ref in zip(ms_list, xs, Y, refs))
                 mb = sum(model_bytes(m.n, m.pairs, vb, xb) for m in ms_list)
                 res[storage] = ms
                 emit({"suite": "C5 batch_256", "storage": storage, "how": how, "members": len(ms_list),
                       "sum_n": tot_n, "sum_pairs": tot_pairs, "ms_per_batch": ms, "GB/s": mb / ms / 1e6,
-                      "GFLOP/s": flops(tot_n, tot_pairs) / ms / 1e6})
+                      "GFLOP/s": flops(tot_n, tot_pairs) / ms / 1e6, "max_rel_err": err,
+                      "tolerance": SUITE_TOL[storage], "cpu_baseline": cpu})
             finally:
                 for h in hs:
                     cs.csrc_destroy(h)
@@ -631,7 +767,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="q1v_96")
-    ap.add_argument("--strategy", default="window", choices=["auto", "window", "atomic"])
+    ap.add_argument("--strategy", default="window", choices=["auto", "window", "window_atomic", "atomic"])
     ap.add_argument("--storage", default="f64", choices=["f64", "f32", "bf16"],
                     help="value storage: f64 (the default workload), or f32 / bf16 with float vectors")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -374,6 +374,78 @@ def test_error_metric_detects_a_dropped_term():
     assert oracle.max_rel_err(m, x, y, y) == 0.0
 
 
+def _lopsided(n, density, seed):
+    """A random structurally symmetric matrix whose upper-triangle values are 1000 times
+    larger than the lower ones, so that the row sums and the column sums of |A| differ."""
+    m = _random_matrix(n, density, seed)
+    rows = np.repeat(np.arange(n), np.diff(m.row_ptr))
+    val = np.where(m.col > rows, 1000.0, 1.0) * m.val
+    return fe.FEMatrix(n, m.row_ptr, m.col, val)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_error_metric_denominator_brute_force(transpose):
+    # the metric of A x divides by the row sums of |A||x|, that of A^T x by the column sums
+    # (the rows of A^T): one perturbed entry at a time, against a dense brute force
+    n = 24
+    m = _lopsided(n, 0.3, 41)
+    x = fe.source_vector(n, 42)
+    dense = np.abs(oracle.dense_rect(n, n, m.row_ptr, m.col, m.val))
+    den = (dense.T if transpose else dense) @ np.abs(x)
+    other = (dense if transpose else dense.T) @ np.abs(x)
+    yref = fe.source_vector(n, 43)
+    checked = 0
+    for i in range(n):
+        if den[i] == 0.0:
+            continue
+        y = yref.copy()
+        y[i] += 1e-3 * den[i]
+        e = oracle.max_rel_err(m, x, y, yref, transpose=transpose)
+        assert e == pytest.approx(1e-3, rel=1e-9)
+        # a denominator of the wrong orientation gives a visibly different value here
+        if abs(other[i] - den[i]) > 0.5 * den[i]:
+            assert abs(1e-3 * den[i] / other[i] - e) > 1e-4
+            checked += 1
+    assert checked > n // 3
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_rect_error_metric_denominator_brute_force(transpose):
+    # the n-by-m form: A x over rows of A, A^T x over columns of A (m outputs)
+    n, mm = 15, 21
+    rng = np.random.default_rng(44)
+    dense = np.where(rng.random((n, mm)) < 0.35, rng.uniform(-1, 1, (n, mm)), 0.0)
+    dense[:, 16] = 0.0  # an empty column: the metric takes the absolute difference there
+    dense *= np.where(np.arange(mm)[None, :] >= n, 1000.0, 1.0)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum((dense != 0).sum(axis=1), out=rp[1:])
+    col = np.nonzero(dense)[1].astype(np.int32)
+    val = dense[dense != 0]
+    xlen, ylen = (n, mm) if transpose else (mm, n)
+    x = fe.source_vector(xlen, 45)
+    den = (np.abs(dense).T if transpose else np.abs(dense)) @ np.abs(x)
+    yref = fe.source_vector(ylen, 46)
+    for i in range(ylen):
+        y = yref.copy()
+        y[i] += 2e-3 * max(den[i], 1.0)
+        e = oracle.max_rel_err_rect(n, mm, rp, col, val, x, y, yref, transpose=transpose)
+        want = 2e-3 * max(den[i], 1.0) / den[i] if den[i] > 0 else 2e-3
+        assert e == pytest.approx(want, rel=1e-9), (i, e, want)
+
+
+def test_error_metric_transpose_detects_a_dropped_term():
+    # a planted mistake in the transposed product: the metric with column sums flags it
+    m = _lopsided(30, 0.25, 47)
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(30, 48)
+    yt = oracle.csrc_spmv_t(c, x)
+    al_bad = c.al.copy()
+    al_bad[len(al_bad) // 3] = 0.0  # A^T x scatters with al: drop one of its terms
+    yt_bad = oracle.csrc_spmv_t(c, x, al=al_bad)
+    assert oracle.max_rel_err(m, x, yt_bad, yt, transpose=True) > 1e-6
+    assert oracle.max_rel_err(m, x, yt, yt, transpose=True) == 0.0
+
+
 # --------------------------------------------------------------------------- Table 1 working sets
 def _table1():
     rows = []
