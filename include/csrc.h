@@ -61,10 +61,12 @@ typedef enum {
   CSRC_ERR_DEVICE_TIMEOUT = 10,      /* a bounded device wait ran out (device status word) */
   CSRC_ERR_DEVICE_BOUNDS = 11,       /* a device-side index check failed (device status word) */
   CSRC_ERR_RANGE = 12,               /* an x value lies outside the double-float range (device status word) */
-  CSRC_ERR_MISMATCH = 13,            /* batch members differ in storage type */
+  CSRC_ERR_MISMATCH = 13,            /* (not returned any more: batch members may differ in storage type) */
   CSRC_ERR_NOT_NUM_SYMMETRIC = 14,   /* CSRC_FLAG_SYMMETRIC_VALUES set but some a_ij != a_ji */
   CSRC_ERR_NOT_CONVERGED = 15,       /* csrc_bicg reached maxit above the tolerance (x = last iterate) */
-  CSRC_ERR_BREAKDOWN = 16            /* csrc_bicg met (r, r*) = 0 or (A p, p*) = 0 (x = last iterate) */
+  CSRC_ERR_BREAKDOWN = 16,           /* csrc_bicg met (r, r*) = 0 or (A p, p*) = 0 (x = last iterate) */
+  CSRC_ERR_NOT_FOUND = 17,           /* csrc_tune_cache_lookup: no entry for this key */
+  CSRC_ERR_IO = 18                   /* the tuning cache file cannot be written */
 } csrc_status;
 
 typedef enum { CSRC_F64 = 0, CSRC_F32 = 1, CSRC_BF16 = 2 } csrc_dtype; /* storage of ad, al, au */
@@ -138,6 +140,9 @@ typedef struct {
   /* the stream-order plan (window-atomic and atomic strategies; 0 before it is built): */
   int32_t stream_nbands;
   int64_t stream_spill_entries;
+  int32_t precision;        /* csrc_dtype of the window strategy's values (csrc_set_precision) */
+  double error_bound;       /* its componentwise error bound (csrc_autotune_precision), 0 before
+                               the window strategy's lists are built */
 } csrc_info;
 
 /*
@@ -294,6 +299,75 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
  * Errors: INVALID_ARG, NOT_PARTITIONED, OUT_OF_MEMORY, CUDA.
  */
 csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream);
+
+/*
+ * Precision of the window strategy's values (the paper computes in FP64; this is the
+ * reduced-precision form of the product). For a CSRC_F64 handle:
+ *   CSRC_F64   (default) FP64 values and FP64 multiply-adds;
+ *   CSRC_F32   every value of the window strategy's lists rounded once to nearest FP32;
+ *   CSRC_BF16  every value rounded once, directly from the double, to nearest-even BF16;
+ * with FP32 / BF16 values, x is rounded to FP32 in the window, the multiply-adds and the
+ * partial sums are FP32, and y is written as double. x and y stay double vectors, so a caller
+ * switches precision without touching its data. The lists are rebuilt at the new precision on
+ * the next product. Only the window strategy (single and batched products, several
+ * right-hand sides) runs at this precision; the other strategies keep the storage's. A
+ * CSRC_F32 / CSRC_BF16 handle accepts only its storage type.
+ * Errors: INVALID_ARG.
+ */
+csrc_status csrc_set_precision(csrc_handle h, csrc_dtype precision);
+
+/*
+ * Pick the cheapest precision of the window strategy that meets a componentwise error
+ * budget: max_i |y_i - (A x)_i| / sum_j |a_ij||x_j| <= max_rel_err for every x. The bound used
+ * is the rounding-error bound of the lists' arithmetic,
+ *   u_v + u_x + (L + P - 1) u_a,
+ * with u_v, u_x, u_a the unit roundoffs of the values, of x in the window and of the
+ * multiply-adds (2^-53 for FP64; 2^-24 for FP32; 2^-8 for BF16 values), L the longest row of A
+ * and P the most partial sums any row is split into across bands. Every precision within the
+ * budget is timed on the caller's device vectors x, y (y is overwritten), and the fastest is
+ * kept (csrc_set_precision). The decision is kept in the tuning cache (csrc_autotune).
+ *   chosen_out  host (nullable): the csrc_dtype picked
+ *   bound_out   host (nullable): its error bound
+ * Synchronous on stream. Errors: INVALID_ARG (null or host pointers, max_rel_err <= 0, or no
+ * precision meets the budget: FP64's own bound is the least attainable), OUT_OF_MEMORY, CUDA.
+ */
+csrc_status csrc_autotune_precision(csrc_handle h, const void* x, void* y, double max_rel_err, int32_t* chosen_out,
+                                    double* bound_out, cudaStream_t stream);
+
+/*
+ * The tuning cache. csrc_autotune, csrc_autotune_spmm and csrc_autotune_precision record
+ * their decisions in a text file keyed by the matrix (its pattern hash, n, nnz, storage and
+ * creation flags) and the device, so that a later process skips the timing. The environment
+ * variable CSRC_TUNE selects the behaviour: "cache" (default) reuses a recorded decision and
+ * tunes and records on a miss; "full" always tunes and records; "off" leaves the handle's
+ * defaults and touches no file. CSRC_TUNE_CACHE names the file (default
+ * $XDG_CACHE_HOME/csrc_gb300/tune.txt, else $HOME/.cache/csrc_gb300/tune.txt). Writes are
+ * whole-file replacements under a lock within the process; lines that do not parse are
+ * ignored.
+ */
+typedef struct {
+  uint64_t pattern_hash; /* FNV-1a 64 of n, ia and ja */
+  int64_t n;
+  int64_t nnz;
+  int32_t storage;       /* csrc_dtype */
+  uint32_t flags;        /* creation flags */
+  char device[64];       /* device name and SM count, NUL-terminated */
+} csrc_tune_key;
+
+enum {
+  CSRC_TUNE_STRATEGY = 0,  /* values: strategy, band count of the window strategy's lists (param 0) */
+  CSRC_TUNE_KTILE = 1,     /* values: columns per pass (param = number of right-hand sides) */
+  CSRC_TUNE_PRECISION = 2  /* values: csrc_dtype (param = error budget) */
+};
+
+/* The cache key of a handle (host only, no device work). Errors: INVALID_ARG. */
+csrc_status csrc_get_tune_key(csrc_handle h, csrc_tune_key* key);
+
+/* Look up / record one decision: values[0..3] (unused ones 0). lookup returns
+ * CSRC_ERR_NOT_FOUND on a miss or when CSRC_TUNE is "off"; store does nothing when it is "off".
+ * Host only. Errors: INVALID_ARG, NOT_FOUND, IO. */
+csrc_status csrc_tune_cache_lookup(const csrc_tune_key* key, int32_t kind, double param, int32_t values[4]);
+csrc_status csrc_tune_cache_store(const csrc_tune_key* key, int32_t kind, double param, const int32_t values[4]);
 
 /* Kernel kinds of csrc_kernel_times. */
 enum {

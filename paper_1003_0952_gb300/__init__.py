@@ -36,6 +36,8 @@ CSRC_ERR_MISMATCH = 13
 CSRC_ERR_NOT_NUM_SYMMETRIC = 14
 CSRC_ERR_NOT_CONVERGED = 15
 CSRC_ERR_BREAKDOWN = 16
+CSRC_ERR_NOT_FOUND = 17
+CSRC_ERR_IO = 18
 
 # storage (csrc_dtype)
 CSRC_F64, CSRC_F32, CSRC_BF16 = 0, 1, 2
@@ -69,11 +71,19 @@ class csrc_info(ctypes.Structure):
         ("block", ctypes.c_int32), ("m", ctypes.c_int64), ("rect_nnz", ctypes.c_int64),
         ("list_entries", ctypes.c_int64), ("list_slices", ctypes.c_int64), ("list_lane_steps", ctypes.c_int64),
         ("list_bytes", ctypes.c_int64), ("stream_nbands", ctypes.c_int32), ("stream_spill_entries", ctypes.c_int64),
+        ("precision", ctypes.c_int32), ("error_bound", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+
+class csrc_tune_key(ctypes.Structure):
+    _fields_ = [("pattern_hash", ctypes.c_uint64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("storage", ctypes.c_int32), ("flags", ctypes.c_uint32), ("device", ctypes.c_char * 64)]
+
+
+CSRC_TUNE_STRATEGY, CSRC_TUNE_KTILE, CSRC_TUNE_PRECISION = 0, 1, 2
 
 # kernel kinds (csrc_kernel_times)
 CSRC_KERNEL_PRODUCT, CSRC_KERNEL_ACCUMULATE, CSRC_KERNEL_OTHER, CSRC_KERNEL_KINDS = 0, 1, 2, 3
@@ -111,6 +121,14 @@ SIGNATURES = {
     "csrc_get_last_device_error": (ctypes.c_int, [_VP]),
     "csrc_destroy": (ctypes.c_int, [_VP]),
     "csrc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "csrc_set_precision": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "csrc_autotune_precision": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _P(ctypes.c_int32),
+                                               _P(ctypes.c_double), _VP]),
+    "csrc_get_tune_key": (ctypes.c_int, [_VP, _P(csrc_tune_key)]),
+    "csrc_tune_cache_lookup": (ctypes.c_int, [_P(csrc_tune_key), ctypes.c_int32, ctypes.c_double,
+                                              _P(ctypes.c_int32)]),
+    "csrc_tune_cache_store": (ctypes.c_int, [_P(csrc_tune_key), ctypes.c_int32, ctypes.c_double,
+                                             _P(ctypes.c_int32)]),
 }
 
 
@@ -291,3 +309,38 @@ def csrc_get_last_device_error(h) -> int:
 
 def csrc_destroy(h) -> None:
     _check(_lib.csrc_destroy(h), "csrc_destroy")
+
+
+def csrc_set_precision(h, precision) -> None:
+    """Precision of the window strategy's values (CSRC_F64, CSRC_F32 or CSRC_BF16)."""
+    _check(_lib.csrc_set_precision(h, int(precision)), "csrc_set_precision")
+
+
+def csrc_autotune_precision(h, x, y, max_rel_err, stream=None) -> tuple[int, float]:
+    """Pick the fastest precision whose error bound meets max_rel_err; returns (precision, bound)."""
+    p = ctypes.c_int32(0)
+    b = ctypes.c_double(0.0)
+    _check(_lib.csrc_autotune_precision(h, _ptr(x), _ptr(y), float(max_rel_err), ctypes.byref(p), ctypes.byref(b),
+                                        _stream(stream)), "csrc_autotune_precision")
+    return p.value, b.value
+
+
+def csrc_get_tune_key(h) -> csrc_tune_key:
+    k = csrc_tune_key()
+    _check(_lib.csrc_get_tune_key(h, ctypes.byref(k)), "csrc_get_tune_key")
+    return k
+
+
+def csrc_tune_cache_lookup(key, kind, param=0.0):
+    """The recorded values (4 ints) for key / kind / param, or None on a miss."""
+    v = (ctypes.c_int32 * 4)()
+    st = _lib.csrc_tune_cache_lookup(ctypes.byref(key), int(kind), float(param), v)
+    if st == CSRC_ERR_NOT_FOUND:
+        return None
+    _check(st, "csrc_tune_cache_lookup")
+    return list(v)
+
+
+def csrc_tune_cache_store(key, kind, param, values) -> None:
+    v = (ctypes.c_int32 * 4)(*[int(a) for a in (list(values) + [0, 0, 0, 0])[:4]])
+    _check(_lib.csrc_tune_cache_store(ctypes.byref(key), int(kind), float(param), v), "csrc_tune_cache_store")

@@ -20,8 +20,8 @@ SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libcsrc_gb300.so")
-SOURCES = ["api.cpp", "owner_plan.cpp", "owner.cu", "kernels.cu", "blocks.cu", "batch.cu", "color.cu", "noalloc.cu",
-           "rect.cu", "solver.cu"]
+SOURCES = ["api.cpp", "owner_plan.cpp", "owner.cu", "owner_batch.cu", "kernels.cu", "blocks.cu", "color.cu",
+           "noalloc.cu", "rect.cu", "solver.cu", "tune.cpp"]
 HEADERS = ["internal.h", "df32.cuh", "band.cuh", "owner.cuh", os.path.join("..", "..", "include", "csrc.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -63,24 +63,30 @@ struct csrc_matrix_s {
   OwnerPlan oplan_rk[3];
   bool have_orp[3] = {false, false, false};
   bool fits_orp[3] = {false, false, false};
-  // owner lists sized for batches (bands of about kBatchBandNnz non-zeros)
-  OwnerPlan oplan_bt;
-  bool have_obt = false;
+  // owner lists sized for batches (bands of about kOwnerBandNnz non-zeros), rk = 1, 2, 4, 8
+  OwnerPlan oplan_bt[4];
+  bool have_obt[4] = {false, false, false, false};
+  bool fits_obt[4] = {false, false, false, false};
   // stream-order plan of the window-atomic and atomic strategies
   DevPlan plan;
   bool have_plan = false;
   bool plan_covers = false;   // every scatter target lies in its band's window
   int32_t part_nbands = 0;    // band count requested for the partition (0 = automatic)
   int32_t owner_nbands = 0;   // band count of the owner plans (0 = automatic; set by the autotuner)
+  // precision of the window strategy's values (csrc_set_precision): the storage type, or FP32 /
+  // BF16 for a CSRC_F64 handle that runs its window products at reduced precision on double vectors
+  int32_t precision = CSRC_F64;
+  int32_t owner_mode() const {
+    if (storage != CSRC_F64) return storage;
+    return precision == CSRC_F32 ? OM_F32_X64 : (precision == CSRC_BF16 ? OM_BF16_X64 : OM_F64);
+  }
+  int64_t max_row_nnz = 0;    // longest row of A (diagonal, lower and upper entries)
+  uint64_t phash = 0;         // pattern hash (tuning cache key)
+  char devname[64] = {0};     // device name and SM count (tuning cache key)
   int32_t block = 1;          // rows per node block found at creation (1 = none)
   DevPlan plan_b1;            // plain-row plan when the main plan uses node blocks
   bool have_b1 = false;
   bool covers_b1 = false;
-  // plan of the batched kernel: bands sized by non-zeros alone (the batch's other members fill
-  // the GPU), built on first use; the matrix never changes, so it is kept until destroy
-  DevPlan plan_bt;
-  bool have_bt = false;
-  bool covers_bt = false;
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
@@ -537,9 +543,8 @@ csrc_status build_owner(csrc_matrix_s* h, int rk, int32_t nbands, OwnerPlan& p, 
   const int32_t nb = nbands > 0 ? std::min<int32_t>(nbands, std::max<int32_t>(1, h->n)) : owner_auto_bands(h, rk);
   std::vector<int32_t> part;
   nnz_partition(h->ia, 0, h->n, nb, part);
-  const int ab = (int)h->xbytes();  // window x and accumulation: double for FP64 storage, else float
-  CSRC_TRY_S(build_owner_plan(h->n, h->h, h->ia, h->ja, part, rk, ab, owner_smem_budget(rk), (int)h->vbytes(), ab,
-                              h->d_al, h->au_ptr(), h->d_ad, h->sym, p));
+  CSRC_TRY_S(build_owner_plan(h->n, h->h, h->ia, h->ja, part, rk, h->owner_mode(), owner_smem_budget(rk),
+                              (int)h->vbytes(), h->d_al, h->au_ptr(), h->d_ad, h->sym, p));
   if (part_out) part_out->swap(part);
   return CSRC_OK;
 }
@@ -551,6 +556,30 @@ void drop_owner_plans(csrc_matrix_s* h) {
     free_owner_plan(h->oplan_rk[i]);
     h->have_orp[i] = h->fits_orp[i] = false;
   }
+  for (int i = 0; i < 4; ++i) {
+    free_owner_plan(h->oplan_bt[i]);
+    h->have_obt[i] = h->fits_obt[i] = false;
+  }
+}
+
+// The owner plan of a batch member for rk columns per pass: bands of about kOwnerBandNnz
+// non-zeros whatever the SM count (the batch's other members fill the GPU; a single
+// product's automatic count would cut each small member into many tiny bands).
+csrc_status owner_batch_for(csrc_matrix_s* h, int rk, OwnerPlan** out) {
+  const int i = rk == 1 ? 0 : (rk == 2 ? 1 : (rk == 4 ? 2 : 3));
+  if (!h->have_obt[i]) {
+    const int64_t nnz = (int64_t)h->n + 2 * h->h;
+    const int64_t nb = std::min<int64_t>(std::max<int64_t>(1, (nnz + kOwnerBandNnz - 1) / kOwnerBandNnz),
+                                         std::max<int32_t>(1, h->n));
+    const csrc_status st = build_owner(h, rk, (int32_t)nb, h->oplan_bt[i], nullptr);
+    if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
+    h->have_obt[i] = true;
+    h->fits_obt[i] = st == CSRC_OK;
+    ++h->generation;
+  }
+  if (!h->fits_obt[i]) return CSRC_ERR_NOT_PARTITIONED;
+  *out = &h->oplan_bt[i];
+  return CSRC_OK;
 }
 
 // The owner plan for rk = 1, 2, 4 or 8 columns per pass, built on first use. Single vectors
@@ -574,6 +603,30 @@ csrc_status owner_for(csrc_matrix_s* h, int rk, OwnerPlan** out) {
   }
   if (!h->fits_orp[i]) return CSRC_ERR_NOT_PARTITIONED;
   *out = &h->oplan_rk[i];
+  return CSRC_OK;
+}
+
+// Componentwise error bound of the window strategy at the handle's precision (relative to
+// sum_j |a_ij||x_j|): u_v + u_x + (L + P - 1) u_a, L the longest row, P the most partial sums of
+// a row (its own band's and the spilled ones), u_v / u_x / u_a the unit roundoffs of the values,
+// of x in the window and of the multiply-adds. Builds the single-vector lists if needed.
+csrc_status owner_error_bound(csrc_matrix_s* h, double* out) {
+  *out = 0.0;
+  if (h->n == 0) return CSRC_OK;
+  OwnerPlan* p = nullptr;
+  CSRC_TRY_S(owner_for(h, 1, &p));
+  const double u53 = std::ldexp(1.0, -53), u24 = std::ldexp(1.0, -24), u8 = std::ldexp(1.0, -8);
+  double uv = 0.0, ux = 0.0, ua = u53;
+  switch (p->mode) {
+    case OM_F64: break;
+    case OM_F32: uv = u24; ua = u24; break;          // x is given as float
+    case OM_BF16: uv = u8; ua = u24; break;
+    case OM_F32_X64: uv = u24; ux = u24; ua = u24; break;
+    default: uv = u8; ux = u24; ua = u24; break;     // OM_BF16_X64
+  }
+  const double terms = (double)h->max_row_nnz + (double)p->max_parts - 1.0;
+  const double g = terms * ua / (1.0 - terms * ua);  // gamma_terms
+  *out = uv + ux + uv * ux + g * (1.0 + uv) * (1.0 + ux);
   return CSRC_OK;
 }
 
@@ -611,24 +664,6 @@ csrc_status plan_b1_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
   }
   *out = &h->plan_b1;
   *covers = h->covers_b1;
-  return CSRC_OK;
-}
-
-// The plan of a batch member: plain rows, about kBatchBandNnz non-zeros per band before
-// windows are fitted. A single product spreads even a small matrix over every SM (the automatic
-// partition makes at least one band per SM); in a batch that would cut each small member into
-// many tiny bands whose set-up dominates, while the members together already fill the GPU.
-constexpr int64_t kBatchBandNnz = 160000;
-csrc_status plan_batch_for(csrc_matrix_s* h, DevPlan** out, bool* covers) {
-  if (!h->have_bt) {
-    const int64_t nnz = (int64_t)h->n + 2 * h->h;
-    const int64_t nb = std::min<int64_t>(std::max<int64_t>(1, (nnz + kBatchBandNnz - 1) / kBatchBandNnz),
-                                         std::max<int32_t>(1, h->n));
-    CSRC_TRY_S(build_plan(h, (int32_t)nb, 1, 1, h->plan_bt, h->covers_bt, nullptr));
-    h->have_bt = true;
-  }
-  *out = &h->plan_bt;
-  *covers = h->covers_bt;
   return CSRC_OK;
 }
 
@@ -739,7 +774,7 @@ BandArgs band_args(const csrc_matrix_s* h, const DevPlan& p, bool transpose, con
 
 // Arguments of one owner-kernel launch on plan p: A x, or A^T x with the exchanged values
 // (Section 5); x and y point at the pass's first column, ldx is their row stride.
-OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y, void* spill, int ldx) {
+OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y, void* spill, int ldx, int lds) {
   OwnerArgs a;
   a.band = p.band;
   a.band_slice = p.band_slice;
@@ -753,6 +788,7 @@ OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y,
   a.y = y;
   a.spill = spill;
   a.ldx = ldx;
+  a.lds = lds;
   a.band_offset = 0;
   return a;
 }
@@ -760,12 +796,12 @@ OwnerArgs owner_args(const OwnerPlan& p, bool transpose, const void* x, void* y,
 // The window strategy on owner plan p: the owner kernel, then the accumulation of spills.
 csrc_status run_owner(csrc_matrix_s* h, const OwnerPlan& p, bool transpose, const void* x, void* y, void* spill,
                       int ldx, int rk, cudaStream_t s) {
-  const OwnerArgs a = owner_args(p, transpose, x, y, spill, ldx);
+  const OwnerArgs a = owner_args(p, transpose, x, y, spill, ldx, rk);
   CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s,
-                        [&] { return launch_owner(h->storage, rk, a, p.nb, p.smem_bytes, s); }));
+                        [&] { return launch_owner(p.mode, rk, a, p.nb, p.smem_bytes, s); }));
   if (p.nacc > 0)
     CSRC_TRY(timed_launch(h, CSRC_KERNEL_ACCUMULATE, s, [&] {
-      return launch_accumulate(h->arith, h->storage, p.nacc, rk, ldx, p.acc_row, p.acc_ptr, nullptr, spill, y, s);
+      return launch_owner_accumulate(p.mode, p.nacc, rk, ldx, p.acc_row, p.acc_ptr, spill, y, s);
     }));
   return CSRC_OK;
 }
@@ -888,11 +924,12 @@ csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, boo
 }
 
 // ---------------------------------------------------------------------------- batched products
-// A batch executor: the (member, band) tiles of a batch of single-vector products, the
-// members' kernel arguments on the device, and the CUDA graph that runs them (memsets of
-// the atomic members' y, one persistent band kernel per (G, strategy) group, one
-// accumulation kernel for every window member). Executors are cached by their arguments
-// and replayed while the members' plans are unchanged.
+// A batch executor. Each member runs at its own mode (storage and precision): members whose
+// strategy is the window strategy become units (member, column chunk of rk columns), whose
+// bands are tiles of one owner-kernel launch per (mode, rk) group, followed by one
+// accumulation launch per mode over all units; members tuned to another strategy run their
+// own launches. The whole sequence is captured in a CUDA graph, cached by its arguments and
+// replayed while the members' plans are unchanged.
 struct BatchExec {
   int device = 0;
   std::vector<csrc_matrix_s*> hs;
@@ -900,18 +937,21 @@ struct BatchExec {
   std::vector<const void*> xs;
   std::vector<void*> ys;
   int transpose = 0;
-  BandArgs* d_members = nullptr;
-  int2* d_tiles = nullptr;
-  int* d_counters = nullptr;
-  AccArgs* d_acc = nullptr;
+  int32_t nrhs = 1;
+  OwnerArgs* d_units = nullptr;
+  OwnerTile* d_tiles = nullptr;
+  OwnerAccArgs* d_acc = nullptr;
   int64_t* d_offs = nullptr;
+  std::vector<void*> spills;  // spill buffers the executor owns (chunks of several columns)
+  std::vector<int32_t> others;  // members that run their own launches after the graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int kernels = 0;  // kernel launches per replay
   ~BatchExec() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    dfree(d_members); dfree(d_tiles); dfree(d_counters); dfree(d_acc); dfree(d_offs);
+    dfree(d_units); dfree(d_tiles); dfree(d_acc); dfree(d_offs);
+    for (void* p : spills) dfree(p);
   }
 };
 
@@ -933,8 +973,9 @@ void drop_batches_of(const csrc_matrix_s* h) {
 }
 
 bool batch_matches(const BatchExec* e, const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
-                   int transpose, int device) {
-  if (e->device != device || e->transpose != transpose || (int32_t)e->hs.size() != batch) return false;
+                   int32_t nrhs, int transpose, int device) {
+  if (e->device != device || e->transpose != transpose || e->nrhs != nrhs || (int32_t)e->hs.size() != batch)
+    return false;
   for (int32_t b = 0; b < batch; ++b)
     if (e->hs[(size_t)b] != hs[b] || e->gens[(size_t)b] != hs[b]->generation || e->xs[(size_t)b] != X[b] ||
         e->ys[(size_t)b] != Y[b])
@@ -942,8 +983,21 @@ bool batch_matches(const BatchExec* e, const csrc_handle* hs, int32_t batch, con
   return true;
 }
 
-csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int transpose,
-                        int device, BatchExec** out) {
+// The column chunks of nrhs columns: the widest pass first (rk = 8, 4, 2, 1, capped by the
+// handle's tuned k-tile), then narrower ones for the remainder.
+std::vector<std::pair<int32_t, int>> column_chunks(const csrc_matrix_s* h, int32_t nrhs) {
+  std::vector<std::pair<int32_t, int>> out;
+  const int cap = h->tuned_rk > 0 ? h->tuned_rk : 8;
+  for (int32_t c0 = 0; c0 < nrhs;) {
+    int rk = 8;
+    while (rk > 1 && (rk > cap || c0 + rk > nrhs)) rk /= 2;
+    out.push_back({c0, rk});
+    c0 += rk;
+  }
+  return out;
+}
+csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int32_t nrhs,
+                        int transpose, int device, BatchExec** out) {
   BatchExec* e = new BatchExec();
   auto fail = [&](csrc_status st) {
     delete e;
@@ -951,17 +1005,17 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
   };
   e->device = device;
   e->transpose = transpose;
-  int sms = 1;
-  std::vector<BandArgs> members((size_t)batch);
-  std::vector<AccArgs> accs;
-  std::vector<int64_t> offs{0};
-  struct Tile { int32_t member, band; int64_t pairs; };
-  std::vector<Tile> groups[4][2];  // [log2 G][atomic]
-  std::vector<std::pair<void*, size_t>> zero_y;
-  int smem = 0;
+  e->nrhs = nrhs;
+  std::vector<int32_t>& others = e->others;
+  struct Unit {
+    const OwnerPlan* p;
+    int mode, rk;
+  };
+  std::vector<Unit> units;
+  std::vector<OwnerArgs> uargs;
+  std::vector<OwnerAccArgs> uacc;
   for (int32_t b = 0; b < batch; ++b) {
     csrc_matrix_s* h = hs[b];
-    sms = std::max(sms, h->sms);
     e->hs.push_back(h);
     e->xs.push_back(X[b]);
     e->ys.push_back(Y[b]);
@@ -970,52 +1024,109 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
       continue;
     }
     if (!is_device_ptr(X[b]) || !is_device_ptr(Y[b])) return fail(CSRC_ERR_INVALID_ARG);
-    const size_t vb = (size_t)h->n * h->xbytes();
+    const size_t vb = (size_t)h->n * (size_t)nrhs * h->xbytes();
     const char* xa = static_cast<const char*>(X[b]);
     const char* ya = static_cast<const char*>(Y[b]);
     if (xa < ya + vb && ya < xa + vb) return fail(CSRC_ERR_ALIAS);
-    DevPlan* p = nullptr;
-    bool covers = false;
-    csrc_status st = plan_batch_for(h, &p, &covers);  // plain rows, bands sized for a batch
-    if (st != CSRC_OK) return fail(st);
-    e->gens.push_back(h->generation);
-    // window strategy whenever the member's windows cover its targets: in a batch the
-    // accumulation launch is shared by all members, so the atomic strategy's gain for a single
-    // small product (one launch fewer) is gone while its zeroing of y (a graph node per
-    // member) remains. Measured on the 256-matrix batch: 0.97 ms with windows for all members
-    // against 1.25 ms with the strategies csrc_autotune picked for single products.
-    const bool atomic = !covers;
-    members[(size_t)b] = band_args(h, *p, transpose != 0, X[b], Y[b], p->spill_buf, 1, 1, atomic);
-    // plans with 16 lanes per row run with 8 in the 512-thread batched kernel (64 groups:
-    // a stage holds at most 64 rows either way)
-    const int lg = p->group == 1 ? 0 : (p->group == 2 ? 1 : (p->group == 4 ? 2 : 3));
-    for (int32_t band = 0; band < p->nb; ++band)
-      groups[lg][atomic ? 1 : 0].push_back({b, band, p->band_pairs[(size_t)band]});
-    smem = std::max(smem, p->smem_bytes);
-    if (atomic) {
-      zero_y.push_back({Y[b], vb});
-    } else if (p->nacc > 0) {
-      accs.push_back({p->acc_row, p->acc_ptr, p->acc_src, p->spill_buf, Y[b]});
-      offs.push_back(offs.back() + p->nacc);
-    }
-  }
-  // tiles, largest bands first within each group
-  std::vector<int2> tiles;
-  struct Launch { int group; bool atomic; int first, count; };
-  std::vector<Launch> launches;
-  for (int lg = 0; lg < 4; ++lg)
-    for (int at = 0; at < 2; ++at) {
-      auto& v = groups[lg][at];
-      if (v.empty()) continue;
-      std::stable_sort(v.begin(), v.end(), [](const Tile& a, const Tile& b) { return a.pairs > b.pairs; });
-      launches.push_back({1 << lg, at != 0, (int)tiles.size(), (int)v.size()});
-      for (const Tile& t : v) {
-        int2 mt;
-        mt.x = t.member;
-        mt.y = t.band;
-        tiles.push_back(mt);
+    // single vectors: the member's tuned strategy; several columns: the window strategy (the
+    // stream-order strategies have no multi-column form)
+    const int strat = h->tuned ? h->tuned : CSRC_STRAT_WINDOW;
+    bool window = nrhs > 1 || strat == CSRC_STRAT_WINDOW;
+    std::vector<std::pair<int32_t, const OwnerPlan*>> chunks;  // (first column, plan)
+    if (window) {
+      std::vector<std::pair<int32_t, int>> todo = column_chunks(h, nrhs);
+      std::reverse(todo.begin(), todo.end());
+      while (window && !todo.empty()) {
+        const auto c = todo.back();
+        todo.pop_back();
+        OwnerPlan* p = nullptr;
+        const csrc_status st = owner_batch_for(h, c.second, &p);
+        if (st == CSRC_OK) {
+          chunks.push_back({c.first, p});
+        } else if (st == CSRC_ERR_NOT_PARTITIONED && c.second > 1) {  // narrower passes fit better
+          todo.push_back({c.first + c.second / 2, c.second / 2});
+          todo.push_back({c.first, c.second / 2});
+        } else if (st == CSRC_ERR_NOT_PARTITIONED && nrhs == 1) {
+          window = false;  // no window holds this member's rows: it runs the atomic strategy
+        } else {
+          return fail(st);
+        }
       }
     }
+    if (!window) {
+      // plans are built now, outside the graph; the member runs its own launches
+      if (strat == CSRC_STRAT_COLOR && h->ncolors == 0) return fail(CSRC_ERR_NOT_COLORED);
+      if (strat != CSRC_STRAT_COLOR && !h->have_plan) {
+        const csrc_status st = make_plan(h);
+        if (st != CSRC_OK) return fail(st);
+      }
+      others.push_back(b);
+      e->gens.push_back(h->generation);
+      continue;
+    }
+    for (const auto& c : chunks) {
+      const OwnerPlan* p = c.second;
+      const int rk = p->rk;
+      void* spill = p->spill_buf;
+      if (nrhs > 1) {  // chunks of one member run at the same time: each has its own spill buffer
+        void* buf = nullptr;
+        if (cudaMalloc(&buf, std::max<size_t>(1, (size_t)p->spill * rk * owner_acc_bytes(p->mode))) != cudaSuccess)
+          return fail(CSRC_ERR_OUT_OF_MEMORY);
+        e->spills.push_back(buf);
+        spill = buf;
+      }
+      const void* xc = static_cast<const char*>(X[b]) + (size_t)c.first * h->xbytes();
+      void* yc = static_cast<char*>(Y[b]) + (size_t)c.first * h->xbytes();
+      units.push_back({p, p->mode, rk});
+      uargs.push_back(owner_args(*p, transpose != 0, xc, yc, spill, nrhs, rk));
+      uacc.push_back({p->acc_row, p->acc_ptr, spill, yc, rk, nrhs});
+    }
+    e->gens.push_back(h->generation);
+  }
+  // tiles grouped by (mode, rk), largest bands first; accumulations grouped by mode
+  struct Group {
+    int mode, rk, first, count, smem;
+  };
+  std::vector<Group> groups;
+  std::vector<OwnerTile> tiles;
+  for (int mode = 0; mode < kOwnerModes; ++mode)
+    for (int rk = 1; rk <= 8; rk *= 2) {
+      std::vector<std::pair<int64_t, OwnerTile>> v;
+      int smem = 16;
+      for (size_t u = 0; u < units.size(); ++u) {
+        if (units[u].mode != mode || units[u].rk != rk) continue;
+        smem = std::max(smem, units[u].p->smem_bytes);
+        for (int32_t band = 0; band < units[u].p->nb; ++band)
+          v.push_back({units[u].p->band_entries[(size_t)band], OwnerTile{(int32_t)u, band, 0, 0}});
+      }
+      if (v.empty()) continue;
+      std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+      groups.push_back({mode, rk, (int)tiles.size(), (int)v.size(), smem});
+      for (const auto& t : v) tiles.push_back(t.second);
+    }
+  struct AccGroup {
+    int mode, first, count, ofirst;
+    int64_t total;
+  };
+  std::vector<AccGroup> agroups;
+  std::vector<OwnerAccArgs> accs;
+  std::vector<int64_t> offs;
+  for (int mode = 0; mode < kOwnerModes; ++mode) {
+    AccGroup g{mode, (int)accs.size(), 0, (int)offs.size(), 0};
+    offs.push_back(0);
+    for (size_t u = 0; u < units.size(); ++u) {
+      if (units[u].mode != mode || units[u].p->nacc == 0) continue;
+      accs.push_back(uacc[u]);
+      g.total += units[u].p->nacc * units[u].rk;
+      offs.push_back(g.total);
+      ++g.count;
+    }
+    if (g.count == 0) {
+      offs.pop_back();
+      continue;
+    }
+    agroups.push_back(g);
+  }
   cudaStream_t s = nullptr;
   cudaError_t ce = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (ce != cudaSuccess) return fail(from_cuda(ce));
@@ -1024,30 +1135,24 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
     if (err != cudaSuccess) return fail(from_cuda(err));
     return CSRC_OK;
   };
-  if ((ce = upload(&e->d_members, members, s)) != cudaSuccess) return done(ce);
+  if ((ce = upload(&e->d_units, uargs, s)) != cudaSuccess) return done(ce);
   if ((ce = upload(&e->d_tiles, tiles, s)) != cudaSuccess) return done(ce);
-  if ((ce = dmalloc(&e->d_counters, std::max<size_t>(1, launches.size()))) != cudaSuccess) return done(ce);
   if ((ce = upload(&e->d_acc, accs, s)) != cudaSuccess) return done(ce);
   if ((ce = upload(&e->d_offs, offs, s)) != cudaSuccess) return done(ce);
   if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) return done(ce);
-  // capture
-  const csrc_matrix_s* h0 = batch > 0 ? hs[0] : nullptr;
   if ((ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return done(ce);
   cudaError_t cap = cudaSuccess;
-  for (auto& z : zero_y)
-    if (cap == cudaSuccess) cap = cudaMemsetAsync(z.first, 0, z.second, s);
-  if (cap == cudaSuccess && !launches.empty()) cap = cudaMemsetAsync(e->d_counters, 0, launches.size() * 4, s);
-  for (size_t i = 0; i < launches.size() && cap == cudaSuccess; ++i) {
-    const Launch& L = launches[i];
-    const int grid = std::min(L.count, sms * BandShape<MODE_DF>::kCtasPerSm);
-    cap = launch_batch_band(h0->arith, h0->storage, L.group, L.atomic, grid, smem, s, e->d_members,
-                            e->d_tiles + L.first, L.count, e->d_counters + i);
+  for (const Group& g : groups) {
+    if (cap != cudaSuccess) break;
+    cap = launch_owner_batch(g.mode, g.rk, e->d_units, e->d_tiles + g.first, g.count, g.smem, s);
     ++e->kernels;
   }
-  if (cap == cudaSuccess && offs.back() > 0) {
-    cap = launch_batch_accumulate(h0->storage, e->d_acc, e->d_offs, (int)accs.size(), offs.back(), s);
+  for (const AccGroup& g : agroups) {
+    if (cap != cudaSuccess) break;
+    cap = launch_owner_batch_accumulate(g.mode, e->d_acc + g.first, e->d_offs + g.ofirst, g.count, g.total, s);
     ++e->kernels;
   }
+  if (groups.empty() && agroups.empty() && cap == cudaSuccess) cap = cudaMemsetAsync(e->d_offs, 0, 0, s);
   ce = cudaStreamEndCapture(s, &e->graph);
   if (cap != cudaSuccess) return done(cap);
   if (ce != cudaSuccess) return done(ce);
@@ -1056,8 +1161,8 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
   return done(cudaSuccess);
 }
 
-csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int transpose,
-                      cudaStream_t stream) {
+csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y, int32_t nrhs,
+                      int transpose, cudaStream_t stream) {
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return CSRC_ERR_CUDA;
   for (int32_t b = 0; b < batch; ++b)
@@ -1065,14 +1170,14 @@ csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X
   std::lock_guard<std::mutex> lk(g_batch_mutex);
   BatchExec* e = nullptr;
   for (size_t i = 0; i < g_batches.size(); ++i)
-    if (batch_matches(g_batches[i], hs, batch, X, Y, transpose, device)) {
+    if (batch_matches(g_batches[i], hs, batch, X, Y, nrhs, transpose, device)) {
       e = g_batches[i];
       g_batches.erase(g_batches.begin() + (long)i);
       g_batches.push_back(e);
       break;
     }
   if (!e) {
-    CSRC_TRY_S(build_batch(hs, batch, X, Y, transpose, device, &e));
+    CSRC_TRY_S(build_batch(hs, batch, X, Y, nrhs, transpose, device, &e));
     if (g_batches.size() >= kMaxBatches) {
       delete g_batches.front();
       g_batches.erase(g_batches.begin());
@@ -1080,8 +1185,18 @@ csrc_status run_batch(const csrc_handle* hs, int32_t batch, const void* const* X
     g_batches.push_back(e);
   }
   csrc_matrix_s* h0 = hs[0];
-  return from_cuda(timed_launch(h0, CSRC_KERNEL_PRODUCT, stream, [&] { return cudaGraphLaunch(e->exec, stream); },
-                                e->kernels));
+  if (e->kernels > 0)
+    CSRC_TRY(timed_launch(h0, CSRC_KERNEL_PRODUCT, stream, [&] { return cudaGraphLaunch(e->exec, stream); },
+                          e->kernels));
+  // single-vector members tuned to another strategy (or whose windows do not fit) run their
+  // own launches on the same stream
+  for (int32_t b : e->others) {
+    csrc_matrix_s* h = hs[b];
+    const int tuned = h->tuned ? h->tuned : CSRC_STRAT_ATOMIC;
+    const csrc_strategy st = (csrc_strategy)(tuned == CSRC_STRAT_WINDOW ? CSRC_STRAT_ATOMIC : tuned);
+    CSRC_TRY_S(run_spmv(h, X[b], Y[b], st, stream, transpose != 0));
+  }
+  return CSRC_OK;
 }
 
 // Rows per node block: the largest B in {3, 2} such that n is a multiple of B and every
@@ -1182,6 +1297,13 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   }
   ia[n] = (int32_t)ja.size();
   const int64_t h64 = (int64_t)ja.size();
+  int64_t max_row_nnz = n > 0 ? 1 : 0;  // diagonal, lower and upper entries of the longest row
+  {
+    std::vector<int32_t> up((size_t)n, 0);
+    for (int32_t k : ja) up[(size_t)k]++;
+    for (int32_t i = 0; i < n; ++i)
+      max_row_nnz = std::max<int64_t>(max_row_nnz, 1 + (int64_t)(ia[(size_t)i + 1] - ia[(size_t)i]) + up[(size_t)i]);
+  }
 
   csrc_matrix_s* m = new (std::nothrow) csrc_matrix_s();
   if (!m) return CSRC_ERR_OUT_OF_MEMORY;
@@ -1189,6 +1311,8 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   m->m = n;
   m->h = h64;
   m->storage = storage;
+  m->precision = storage;
+  m->max_row_nnz = max_row_nnz;
   m->flags = flags;
   m->block = (flags & CSRC_FLAG_NODE_BLOCKS) ? detect_node_blocks(n, ia, ja) : 1;
   if (flags & CSRC_FLAG_SYMMETRIC_VALUES) {
@@ -1202,6 +1326,14 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   cudaGetDevice(&m->device);
   cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
   if (m->sms <= 0) m->sms = 1;
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, m->device) == cudaSuccess)
+      std::snprintf(m->devname, sizeof(m->devname), "%.48s/%dSM", prop.name, m->sms);
+    else
+      cudaGetLastError();
+  }
+  m->phash = pattern_hash(n, ia, ja);
   if (storage == CSRC_F64) {
     // FP64 arithmetic unless double-float is asked for (stream-order strategies only)
     m->arith = ((flags & CSRC_FLAG_DF32_ARITH) && !(flags & CSRC_FLAG_FP64_ARITH)) ? ARITH_DF32 : ARITH_F64;
@@ -1282,8 +1414,7 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   {
     std::lock_guard<std::mutex> lk(g_setup_mutex);
     if (!g_prepared) {
-      if (prepare_band_kernels() != cudaSuccess || prepare_batch_kernels() != cudaSuccess ||
-          prepare_owner_kernels() != cudaSuccess) {
+      if (prepare_band_kernels() != cudaSuccess || prepare_owner_kernels() != cudaSuccess) {
         cudaGetLastError();
         return fail(CSRC_ERR_CUDA);
       }
@@ -1316,10 +1447,9 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
   if (h->oplan.spill > capacity) return CSRC_ERR_INVALID_ARG;
   if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
   const OwnerPlan& p = h->oplan;
-  const OwnerArgs a = owner_args(p, transpose, x, y, spill, 1);
-  CSRC_TRY(launch_owner(h->storage, 1, a, p.nb, p.smem_bytes, s));
-  if (p.nacc > 0)
-    CSRC_TRY(launch_accumulate(h->arith, h->storage, p.nacc, 1, 1, p.acc_row, p.acc_ptr, nullptr, spill, y, s));
+  const OwnerArgs a = owner_args(p, transpose, x, y, spill, 1, 1);
+  CSRC_TRY(launch_owner(p.mode, 1, a, p.nb, p.smem_bytes, s));
+  if (p.nacc > 0) CSRC_TRY(launch_owner_accumulate(p.mode, p.nacc, 1, 1, p.acc_row, p.acc_ptr, spill, y, s));
   return CSRC_OK;
 }
 
@@ -1638,16 +1768,15 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
   for (int32_t b = 0; b < batch; ++b) {
     if (!hs[b] || !X[b] || !Y[b]) return CSRC_ERR_INVALID_ARG;
     if (hs[b]->rect()) return CSRC_ERR_INVALID_ARG;  // rectangular matrices run single products
-    if (hs[b]->storage != hs[0]->storage) return CSRC_ERR_MISMATCH;
   }
   if (batch == 0) return CSRC_OK;
   try {
-    if (nrhs == 1) return run_batch(hs, batch, X, Y, transpose != 0 ? 1 : 0, stream);
-    for (int32_t b = 0; b < batch; ++b) CSRC_TRY_S(spmm_one(hs[b], X[b], Y[b], nrhs, transpose != 0, stream));
+    DeviceGuard dg;
+    CSRC_TRY_S(dg.enter(hs[0]));
+    return run_batch(hs, batch, X, Y, nrhs, transpose != 0 ? 1 : 0, stream);
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
   }
-  return CSRC_OK;
 }
 
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream) {
@@ -1657,6 +1786,22 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
   CSRC_TRY_S(dg.enter(h));
   if (h->n == 0) {
     h->tuned = CSRC_STRAT_WINDOW;
+    return CSRC_OK;
+  }
+  const int mode = tune_mode();
+  if (mode == TUNE_OFF) return CSRC_OK;
+  csrc_tune_key key;
+  csrc_get_tune_key(h, &key);
+  int32_t cached[4] = {0, 0, 0, 0};
+  if (mode == TUNE_CACHE && csrc_tune_cache_lookup(&key, CSRC_TUNE_STRATEGY, 0.0, cached) == CSRC_OK &&
+      cached[0] >= CSRC_STRAT_WINDOW && cached[0] <= CSRC_STRAT_WINDOW_ATOMIC && cached[1] >= 0 &&
+      (cached[0] != CSRC_STRAT_COLOR || h->ncolors > 0)) {
+    if (h->owner_nbands != cached[1]) {
+      h->owner_nbands = cached[1];
+      drop_owner_plans(h);
+    }
+    h->tuned = cached[0];
+    ++h->generation;
     return CSRC_OK;
   }
   try {
@@ -1721,6 +1866,8 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
     }
     h->tuned = best_st;
     ++h->generation;
+    const int32_t v[4] = {best_st, best_nb, 0, 0};
+    csrc_tune_cache_store(&key, CSRC_TUNE_STRATEGY, 0.0, v);
     return CSRC_OK;
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
@@ -1732,6 +1879,17 @@ csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nr
   DeviceGuard dg;
   CSRC_TRY_S(dg.enter(h));
   if (h->n == 0 || nrhs == 1) return CSRC_OK;
+  const int mode = tune_mode();
+  if (mode == TUNE_OFF) return CSRC_OK;
+  csrc_tune_key key;
+  csrc_get_tune_key(h, &key);
+  int32_t cached[4] = {0, 0, 0, 0};
+  if (mode == TUNE_CACHE && csrc_tune_cache_lookup(&key, CSRC_TUNE_KTILE, (double)nrhs, cached) == CSRC_OK &&
+      (cached[0] == 1 || cached[0] == 2 || cached[0] == 4 || cached[0] == 8)) {
+    h->tuned_rk = cached[0];
+    ++h->generation;
+    return CSRC_OK;
+  }
   try {
     const bool prof = h->profiling;
     h->profiling = false;
@@ -1769,7 +1927,105 @@ csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nr
     h->profiling = prof;
     h->tuned_rk = best_rk;
     ++h->generation;
+    if (st == CSRC_OK && best_rk > 0) {
+      const int32_t v[4] = {best_rk, 0, 0, 0};
+      csrc_tune_cache_store(&key, CSRC_TUNE_KTILE, (double)nrhs, v);
+    }
     return st;
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_get_tune_key(csrc_handle h, csrc_tune_key* key) {
+  if (!h || !key) return CSRC_ERR_INVALID_ARG;
+  std::memset(key, 0, sizeof(*key));
+  key->pattern_hash = h->phash;
+  key->n = h->n;
+  key->nnz = (int64_t)h->n + 2 * h->h;
+  key->storage = h->storage;
+  key->flags = h->flags;
+  std::memcpy(key->device, h->devname, sizeof(key->device));
+  key->device[sizeof(key->device) - 1] = 0;
+  return CSRC_OK;
+}
+
+csrc_status csrc_set_precision(csrc_handle h, csrc_dtype precision) {
+  if (!h) return CSRC_ERR_INVALID_ARG;
+  if (precision < CSRC_F64 || precision > CSRC_BF16) return CSRC_ERR_INVALID_ARG;
+  if (h->storage != CSRC_F64 && precision != h->storage) return CSRC_ERR_INVALID_ARG;
+  if (h->precision == precision) return CSRC_OK;
+  drop_batches_of(h);
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
+  cudaDeviceSynchronize();  // products in flight may still read the lists being replaced
+  h->precision = precision;
+  drop_owner_plans(h);
+  ++h->generation;
+  return CSRC_OK;
+}
+
+csrc_status csrc_autotune_precision(csrc_handle h, const void* x, void* y, double max_rel_err, int32_t* chosen_out,
+                                    double* bound_out, cudaStream_t stream) {
+  if (!h || !x || !y || !(max_rel_err > 0.0) || h->rect()) return CSRC_ERR_INVALID_ARG;
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return CSRC_ERR_INVALID_ARG;
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
+  try {
+    const int mode = tune_mode();
+    csrc_tune_key key;
+    csrc_get_tune_key(h, &key);
+    int32_t cached[4] = {0, 0, 0, 0};
+    if (mode == TUNE_CACHE && csrc_tune_cache_lookup(&key, CSRC_TUNE_PRECISION, max_rel_err, cached) == CSRC_OK &&
+        cached[0] >= CSRC_F64 && cached[0] <= CSRC_BF16 && (h->storage == CSRC_F64 || cached[0] == h->storage)) {
+      CSRC_TRY_S(csrc_set_precision(h, (csrc_dtype)cached[0]));
+    } else if (mode != TUNE_OFF) {
+      // candidates in the handle's reach, cheapest bytes first
+      std::vector<csrc_dtype> cands;
+      if (h->storage == CSRC_F64) cands = {CSRC_BF16, CSRC_F32, CSRC_F64};
+      else cands = {h->storage};
+      const bool prof = h->profiling;
+      h->profiling = false;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      CSRC_TRY(cudaEventCreate(&e0));
+      CSRC_TRY(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int32_t best_p = -1;
+      csrc_status st = CSRC_OK;
+      for (csrc_dtype p : cands) {
+        if ((st = csrc_set_precision(h, p)) != CSRC_OK) break;
+        double bound = 0.0;
+        if ((st = owner_error_bound(h, &bound)) != CSRC_OK) break;
+        if (bound > max_rel_err) continue;
+        if ((st = run_spmv(h, x, y, CSRC_STRAT_WINDOW, stream, false)) != CSRC_OK) break;  // warm-up
+        cudaError_t ce = cudaEventRecord(e0, stream);
+        for (int i = 0; i < 5 && st == CSRC_OK && ce == cudaSuccess; ++i)
+          st = run_spmv(h, x, y, CSRC_STRAT_WINDOW, stream, false);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) st = from_cuda(ce);
+        if (st != CSRC_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_p = p;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      h->profiling = prof;
+      if (st != CSRC_OK) return st;
+      if (best_p < 0) return CSRC_ERR_INVALID_ARG;  // not even FP64 meets the budget
+      CSRC_TRY_S(csrc_set_precision(h, (csrc_dtype)best_p));
+      const int32_t v[4] = {best_p, 0, 0, 0};
+      csrc_tune_cache_store(&key, CSRC_TUNE_PRECISION, max_rel_err, v);
+    }
+    double bound = 0.0;
+    CSRC_TRY_S(owner_error_bound(h, &bound));
+    if (chosen_out) *chosen_out = h->precision;
+    if (bound_out) *bound_out = bound;
+    return CSRC_OK;
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
   }
@@ -1926,6 +2182,8 @@ csrc_status csrc_get_info(csrc_handle h, csrc_info* info) {
                        4 * p.spill + xb * ((int64_t)h->n + p.spill) + xb * h->n + xb * p.spill;
   }
   info->ncolors = h->ncolors;
+  info->precision = h->precision;
+  if (h->have_oplan) owner_error_bound(h, &info->error_bound);
   info->tuned_strategy = h->tuned;
   info->tuned_rk = h->tuned_rk;
   info->group = h->have_plan ? h->plan.group : 0;
@@ -1960,9 +2218,7 @@ csrc_status csrc_destroy(csrc_handle h) {
   cudaDeviceSynchronize();
   free_plan(h->plan);
   drop_owner_plans(h);
-  free_owner_plan(h->oplan_bt);
   free_plan(h->plan_b1);
-  free_plan(h->plan_bt);
   dfree(h->d_ia); dfree(h->d_ja); dfree(h->d_al); dfree(h->d_au); dfree(h->d_ad);
   dfree(h->d_al_df); dfree(h->d_au_df);
   dfree(h->d_rrow); dfree(h->d_rptr); dfree(h->d_rcol); dfree(h->d_rval);
@@ -1990,10 +2246,12 @@ const char* csrc_status_string(csrc_status st) {
     case CSRC_ERR_DEVICE_TIMEOUT: return "bounded device wait ran out";
     case CSRC_ERR_DEVICE_BOUNDS: return "device index check failed";
     case CSRC_ERR_RANGE: return "x value outside the double-float range";
-    case CSRC_ERR_MISMATCH: return "batch members differ in storage type";
+    case CSRC_ERR_MISMATCH: return "storage type mismatch";
     case CSRC_ERR_NOT_NUM_SYMMETRIC: return "symmetric-value storage requested but a_ij != a_ji";
     case CSRC_ERR_NOT_CONVERGED: return "iteration limit reached above the tolerance";
     case CSRC_ERR_BREAKDOWN: return "BiCG breakdown: a zero inner product";
+    case CSRC_ERR_NOT_FOUND: return "no tuning cache entry for this key";
+    case CSRC_ERR_IO: return "the tuning cache file cannot be written";
   }
   return "unknown status";
 }

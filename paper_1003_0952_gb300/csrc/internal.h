@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include <cuda_runtime_api.h>
@@ -172,6 +173,17 @@ constexpr uint32_t kOwnerPadSlot = 0xffffu;  // lane word slot of an unused lane
 constexpr int kOwnerMaxSlots = 65535;         // slots are 16-bit; 0xffff marks unused lanes
 constexpr int kOwnerMaxLength = 65535;        // list lengths are 16-bit
 
+// Arithmetic modes of the owner kernel: the storage of the listed values and the type of x
+// and y. Modes 0-2 are the handle's storage types (FP64: FP64 arithmetic; FP32 / BF16: FP32
+// arithmetic on float vectors). Modes 3-4 serve a CSRC_F64 handle whose window strategy runs at
+// a reduced precision (csrc_set_precision): values rounded to FP32 / BF16, x rounded to FP32 in
+// the window, FP32 multiply-adds, y written as double.
+enum OwnerMode : int { OM_F64 = 0, OM_F32 = 1, OM_BF16 = 2, OM_F32_X64 = 3, OM_BF16_X64 = 4 };
+constexpr int kOwnerModes = 5;
+inline int owner_value_bytes(int mode) { return mode == OM_F64 ? 8 : ((mode == OM_F32 || mode == OM_F32_X64) ? 4 : 2); }
+inline int owner_acc_bytes(int mode) { return mode == OM_F64 ? 8 : 4; }   // window x, sums, spill
+inline int owner_vec_bytes(int mode) { return (mode == OM_F64 || mode >= OM_F32_X64) ? 8 : 4; }  // x, y
+
 // Kernel shape: threads per CTA and CTAs per SM the window budget is sized for.
 constexpr int kOwnerThreads = 256;
 inline int owner_ctas_per_sm(int rk) { return rk <= 1 ? 4 : (rk <= 2 ? 2 : 1); }
@@ -180,6 +192,9 @@ inline int owner_smem_budget(int rk) { return smem_limit_for(owner_ctas_per_sm(r
 struct OwnerPlan {
   int32_t nb = 0;            // bands
   int32_t rk = 1;            // columns per pass the windows are sized for
+  int32_t mode = OM_F64;     // OwnerMode of the values
+  int32_t max_len = 0;       // longest entry list
+  int32_t max_parts = 1;     // most partial sums of one row (its own band's and the spilled ones)
   int64_t entries = 0;       // list entries of all bands (n + 2h)
   int64_t lane_steps = 0;    // sum over slices of 32 * longest list (FMA lanes issued)
   int64_t nslices = 0;
@@ -219,7 +234,13 @@ struct OwnerArgs {
   void* y;
   void* spill;
   int32_t ldx;        // row stride of x and y in elements (the pass's columns start at x, y)
+  int32_t lds;        // row stride of the spill buffer in elements (the pass's columns start at spill)
   int32_t band_offset;
+};
+
+// One tile of a batched launch: band `band` of member `member`, columns [col0, col0 + RK).
+struct OwnerTile {
+  int32_t member, band, col0, pad;
 };
 
 // Host side of the owner plan (owner_plan.cpp). Builds the lists of the bands of `part`
@@ -228,19 +249,43 @@ struct OwnerArgs {
 // gathered on the device from al / au / ad (storage type of vbytes bytes per value).
 // Returns CSRC_ERR_NOT_PARTITIONED when a list is longer than 65,535 entries or a single
 // row's window does not fit.
+// The handle's al / au / ad are of `in_bytes` bytes per value (8 = double, 4 = float, 2 = BF16);
+// the lists hold the values of `mode` (a double is rounded to nearest-even when the mode's
+// values are narrower).
 csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& ia, const std::vector<int32_t>& ja,
-                             const std::vector<int32_t>& part, int rk, int slot_bytes, int budget, int vbytes,
-                             int spill_bytes, const void* al, const void* au, const void* ad, bool sym,
-                             OwnerPlan& out);
+                             const std::vector<int32_t>& part, int rk, int mode, int budget, int in_bytes,
+                             const void* al, const void* au, const void* ad, bool sym, OwnerPlan& out);
 void free_owner_plan(OwnerPlan& p);
 
-// Launchers (owner.cu).
+// Launchers (owner.cu, owner_batch.cu).
 cudaError_t prepare_owner_kernels();
 // out_a[e] / out_t[e] = the value of entry e for A x / A^T x, from its source code
-// (k << 2 | kind, kind 0 = ad[k], 1 = al[k], 2 = au[k]); vbytes = 8, 4 or 2.
-cudaError_t launch_owner_gather(int vbytes, const int64_t* code, int64_t count, const void* al, const void* au,
-                                const void* ad, void* out_a, void* out_t, cudaStream_t s);
-cudaError_t launch_owner(int storage, int rk, const OwnerArgs& a, int nbands, int smem, cudaStream_t s);
+// (k << 2 | kind, kind 0 = ad[k], 1 = al[k], 2 = au[k]); sources of in_bytes bytes per value,
+// outputs of out_bytes (8 -> 4: round to nearest FP32; 8 -> 2: round to nearest-even BF16 directly).
+cudaError_t launch_owner_gather(int in_bytes, int out_bytes, const int64_t* code, int64_t count, const void* al,
+                                const void* au, const void* ad, void* out_a, void* out_t, cudaStream_t s);
+cudaError_t launch_owner(int mode, int rk, const OwnerArgs& a, int nbands, int smem, cudaStream_t s);
+// Batched: one CTA per tile, member arguments on the device.
+cudaError_t prepare_owner_batch_kernels();
+cudaError_t launch_owner_batch(int mode, int rk, const OwnerArgs* members, const OwnerTile* tiles, int ntiles,
+                               int smem, cudaStream_t s);
+// y[row, c] += the row's spilled sums, for the owner plans' row-ordered spill buffers: y of the
+// mode's vector type, spill of its accumulation type (rk columns, row stride ldx in y and rk in spill).
+cudaError_t launch_owner_accumulate(int mode, int64_t nacc, int rk, int ldx, const int32_t* acc_row,
+                                    const int32_t* acc_ptr, const void* spill, void* y, cudaStream_t s);
+// Accumulation arguments of one member of a batch (row-ordered spill buffer, rk columns).
+struct OwnerAccArgs {
+  const int32_t* acc_row;
+  const int32_t* acc_ptr;
+  const void* spill;
+  void* y;
+  int32_t rk;
+  int32_t ldx;
+};
+// Every member's accumulation in one launch: members of one mode; offs[m] = first (row, column)
+// item of member m (offs[nmembers] = total items).
+cudaError_t launch_owner_batch_accumulate(int mode, const OwnerAccArgs* members, const int64_t* offs,
+                                          int nmembers, int64_t total, cudaStream_t s);
 
 // Arguments of the band kernels (passed by value).
 struct BandArgs {
@@ -276,14 +321,12 @@ struct BandArgs {
   int32_t band_offset;
 };
 
-// Accumulation arguments of one batch member (spill -> y).
-struct AccArgs {
-  const int32_t* acc_row;
-  const int32_t* acc_ptr;
-  const int32_t* acc_src;
-  const void* spill;
-  void* y;
-};
+// Tuning cache (tune.cpp): CSRC_TUNE = off / cache (default) / full, the cache file, and the
+// pattern hash of a matrix.
+enum { TUNE_OFF = 0, TUNE_CACHE = 1, TUNE_FULL = 2 };
+int tune_mode();
+std::string tune_cache_path();
+uint64_t pattern_hash(int32_t n, const std::vector<int32_t>& ia, const std::vector<int32_t>& ja);
 
 // Device status bits (OR-ed by kernels, read by csrc_get_last_device_error).
 enum : int32_t { DEV_RANGE = 1, DEV_TIMEOUT = 2, DEV_BOUNDS = 4 };
@@ -319,13 +362,6 @@ cudaError_t launch_wait_probe(long long limit, int32_t* status, cudaStream_t s);
 cudaError_t prepare_band_kernels();
 cudaError_t prepare_band_kernels_block();
 cudaError_t launch_band_block(Arith arith, int storage, const BandArgs& a, int nbands, int smem, cudaStream_t s);
-
-// Batched products (batch.cu).
-cudaError_t prepare_batch_kernels();
-cudaError_t launch_batch_band(Arith arith, int storage, int group, bool atomic, int grid, int smem, cudaStream_t s,
-                              const BandArgs* members, const int2* tiles, int ntiles, int* next_tile);
-cudaError_t launch_batch_accumulate(int storage, const AccArgs* members, const int64_t* offs, int nmembers,
-                                    int64_t total, cudaStream_t s);
 
 // Product into caller-provided spill memory, allocating nothing (api.cpp; used by noalloc.cu).
 int32_t handle_device(const csrc_matrix_s* h);

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -44,6 +45,18 @@ template <>
 struct OwnerTypes<CSRC_BF16> {
   using V = uint16_t;  // BF16 bits
   using X = float;
+  using A = float;
+};
+template <>
+struct OwnerTypes<OM_F32_X64> {  // reduced precision on double vectors
+  using V = float;
+  using X = double;
+  using A = float;
+};
+template <>
+struct OwnerTypes<OM_BF16_X64> {
+  using V = uint16_t;
+  using X = double;
   using A = float;
 };
 
@@ -228,7 +241,7 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
       owner_fma_batch<A, V, U, RK>(xs, m0, len, sv, vv, acc);
     }
     if (slot < nsp) {
-      A* sp = static_cast<A*>(a.spill) + (size_t)__ldg(a.spill_pos + sbase + slot) * RK;
+      A* sp = static_cast<A*>(a.spill) + (size_t)__ldg(a.spill_pos + sbase + slot) * a.lds;
 #pragma unroll
       for (int c = 0; c < RK; ++c) sp[c] = acc[c];
     } else if (slot != (int)kOwnerPadSlot) {

@@ -217,10 +217,11 @@ void free_owner_plan(OwnerPlan& p) {
 }
 
 csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& ia, const std::vector<int32_t>& ja,
-                             const std::vector<int32_t>& part, int rk, int slot_bytes, int budget, int vbytes,
-                             int spill_bytes, const void* al, const void* au, const void* ad, bool sym,
-                             OwnerPlan& out) {
+                             const std::vector<int32_t>& part, int rk, int mode, int budget, int in_bytes,
+                             const void* al, const void* au, const void* ad, bool sym, OwnerPlan& out) {
   (void)h;
+  const int slot_bytes = owner_acc_bytes(mode), spill_bytes = owner_acc_bytes(mode);
+  const int vbytes = owner_value_bytes(mode);
   free_owner_plan(out);
   const int workers = std::max(1, std::min<int>(worker_count(), n / 4096 + 1));
   // ---- pass 1: bands whose windows fit (in partition order)
@@ -302,6 +303,8 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   OwnerPlan p;
   p.nb = nb;
   p.rk = rk;
+  p.mode = mode;
+  for (int64_t q = 0; q < nslices; ++q) p.max_len = std::max<int32_t>(p.max_len, (int32_t)(lane[(size_t)q * kOwnerLanes] >> 16));
   p.entries = entries;
   p.nslices = nslices;
   p.spill = spill;
@@ -309,6 +312,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   p.smem_bytes = std::max(16, max_slots * slot_bytes * rk);
   for (int64_t v : steps) p.lane_steps += v;
   p.nacc = (int64_t)acc_row.size();
+  for (size_t i = 0; i + 1 < acc_ptr.size(); ++i) p.max_parts = std::max(p.max_parts, 1 + acc_ptr[i + 1] - acc_ptr[i]);
   p.band_entries.resize((size_t)nb);
   for (int32_t b = 0; b < nb; ++b)
     p.band_entries[(size_t)b] = L.band_entry[(size_t)b + 1] - L.band_entry[(size_t)b];
@@ -335,7 +339,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   if (e == cudaSuccess && !sym) e = cudaMalloc(&p.VT, std::max<size_t>(1, (size_t)entries * (size_t)vbytes));
   if (e == cudaSuccess && sym) p.VT = p.VA;
   if (e == cudaSuccess)
-    e = launch_owner_gather(vbytes, dcode, entries, al, sym ? al : au, ad, p.VA, sym ? nullptr : p.VT, 0);
+    e = launch_owner_gather(in_bytes, vbytes, dcode, entries, al, sym ? al : au, ad, p.VA, sym ? nullptr : p.VT, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (dcode) cudaFree(dcode);
   if (e != cudaSuccess) {

@@ -47,7 +47,7 @@ def test_library_exports_every_declared_symbol(cs):
 
 
 def test_status_strings(cs):
-    for st in range(0, 14):
+    for st in range(0, 19):
         s = cs.csrc_status_string(st)
         assert s and s != "unknown status"
     assert cs.csrc_status_string(99) == "unknown status"

@@ -153,7 +153,7 @@ def test_batched_single_vectors_graph_replay(cs, storage):
             cs.csrc_destroy(h)
 
 
-def test_batched_integer_exact_and_mismatch(cs):
+def test_batched_integer_exact_and_mixed_storage(cs):
     ms = [fe.p1_grid(11, 9, 1), fe.q1_hex(5, 3, 2), fe.tet_mesh(1500, 3, method="kuhn")]
     ims = [fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 5)) for m in ms]
     hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64) for m in ims]
@@ -165,11 +165,16 @@ def test_batched_integer_exact_and_mismatch(cs):
         torch.cuda.synchronize()
         for m, x, y in zip(ims, xs, Yd):
             np.testing.assert_array_equal(y.cpu().numpy(), oracle.csrc_spmv(oracle.from_matrix(m), x))
+        # members of different storage types share one batch (each with its own vector type)
         h32 = cs.csrc_create_from_csr(ims[0].n, ims[0].row_ptr, ims[0].col, ims[0].val, cs.CSRC_F32)
         try:
-            with pytest.raises(cs.CsrcError) as e:
-                cs.csrc_spmm_batched([hs[0], h32], Xd[:1] * 2, Yd[:1] * 2, 1, False)
-            assert e.value.status == cs.CSRC_ERR_MISMATCH
+            x32 = Xd[0].float()
+            y32 = torch.empty_like(x32)
+            cs.csrc_spmm_batched([hs[0], h32], [Xd[0], x32], [Yd[0], y32], 1, False)
+            torch.cuda.synchronize()
+            ref = oracle.csrc_spmv(oracle.from_matrix(ims[0]), xs[0])
+            np.testing.assert_array_equal(Yd[0].cpu().numpy(), ref)
+            np.testing.assert_array_equal(y32.cpu().numpy().astype(np.float64), ref)
         finally:
             cs.csrc_destroy(h32)
     finally:
@@ -177,10 +182,9 @@ def test_batched_integer_exact_and_mismatch(cs):
             cs.csrc_destroy(h)
 
 
-def test_batched_member_without_cover_runs_atomic(cs):
-    # the last row couples to one row in each of 400 window pages: no shared-memory window holds
-    # its targets, so that member's plan overflows and the batch runs it with the atomic
-    # strategy, next to members that use windows; integer values make every result exact
+def test_batched_member_with_a_wide_row(cs):
+    # the last row couples to one row in each of 400 window pages of 64 rows: a wide window,
+    # next to small members; integer values make every result exact
     n = 64 * 400
     ei = np.concatenate([np.arange(1, n), np.full(400, n - 1)])
     ej = np.concatenate([np.arange(0, n - 1), np.arange(0, n - 1, 64)])  # 400 rows, one per page
