@@ -67,6 +67,7 @@ struct csrc_matrix_s {
   OwnerPlan oplan_bt[4];
   bool have_obt[4] = {false, false, false, false};
   bool fits_obt[4] = {false, false, false, false};
+  int64_t obt_target[4] = {0, 0, 0, 0};  // non-zeros per band the batch plans were built for
   // stream-order plan of the window-atomic and atomic strategies
   DevPlan plan;
   bool have_plan = false;
@@ -531,6 +532,12 @@ csrc_status build_plan(csrc_matrix_s* h, int32_t nbands, int rk, int B, DevPlan&
 constexpr int64_t kOwnerBandNnz = 100000;
 int32_t owner_auto_bands(const csrc_matrix_s* h, int rk) {
   const int64_t nnz = (int64_t)h->n + 2 * h->h;
+  if (rk > 1) {
+    // wider passes: the window size splits the bands much further anyway; start from bands of
+    // kOwnerBandNnz non-zeros and let the splits decide (measured faster than whole waves here)
+    return (int32_t)std::min<int64_t>(std::max<int64_t>(1, (nnz + kOwnerBandNnz - 1) / kOwnerBandNnz),
+                                      std::max<int32_t>(1, h->n));
+  }
   const int64_t slots = (int64_t)h->sms * owner_ctas_per_sm(rk);
   int64_t waves = (nnz + slots * kOwnerBandNnz - 1) / (slots * kOwnerBandNnz);
   if (waves < 1) waves = 1;
@@ -562,14 +569,19 @@ void drop_owner_plans(csrc_matrix_s* h) {
   }
 }
 
-// The owner plan of a batch member for rk columns per pass: bands of about kOwnerBandNnz
-// non-zeros whatever the SM count (the batch's other members fill the GPU; a single
-// product's automatic count would cut each small member into many tiny bands).
-csrc_status owner_batch_for(csrc_matrix_s* h, int rk, OwnerPlan** out) {
+// The owner plan of a batch member for rk columns per pass: bands of about band_nnz non-zeros
+// whatever the SM count (the batch's other members fill the GPU; a single product's automatic
+// count would cut each small member into many tiny bands). Rebuilt when band_nnz changes.
+csrc_status owner_batch_for(csrc_matrix_s* h, int rk, int64_t band_nnz, OwnerPlan** out) {
   const int i = rk == 1 ? 0 : (rk == 2 ? 1 : (rk == 4 ? 2 : 3));
+  if (h->have_obt[i] && h->obt_target[i] != band_nnz) {
+    free_owner_plan(h->oplan_bt[i]);
+    h->have_obt[i] = false;
+  }
   if (!h->have_obt[i]) {
+    h->obt_target[i] = band_nnz;
     const int64_t nnz = (int64_t)h->n + 2 * h->h;
-    const int64_t nb = std::min<int64_t>(std::max<int64_t>(1, (nnz + kOwnerBandNnz - 1) / kOwnerBandNnz),
+    const int64_t nb = std::min<int64_t>(std::max<int64_t>(1, (nnz + band_nnz - 1) / band_nnz),
                                          std::max<int32_t>(1, h->n));
     const csrc_status st = build_owner(h, rk, (int32_t)nb, h->oplan_bt[i], nullptr);
     if (st != CSRC_OK && st != CSRC_ERR_NOT_PARTITIONED) return st;
@@ -891,38 +903,6 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
   return CSRC_OK;
 }
 
-// Y = A X (or A^T X) for one handle, X and Y n-by-nrhs row-major device blocks: the
-// columns are cut into passes of rk = 8, 4, 2 or 1 columns (the handle's tuned k-tile caps
-// rk; a pass falls back to fewer columns when no window of rk columns fits), and each pass
-// runs the owner kernel and the accumulation kernel on its columns.
-csrc_status spmm_one(csrc_matrix_s* h, const void* X, void* Y, int32_t nrhs, bool transpose, cudaStream_t s) {
-  if (h->n == 0) return CSRC_OK;
-  const size_t vb = (size_t)h->n * (size_t)nrhs * h->xbytes();
-  const char* xa = static_cast<const char*>(X);
-  const char* ya = static_cast<const char*>(Y);
-  if (xa < ya + vb && ya < xa + vb) return CSRC_ERR_ALIAS;
-  if (!is_device_ptr(X) || !is_device_ptr(Y)) return CSRC_ERR_INVALID_ARG;
-  DeviceGuard dg;
-  CSRC_TRY_S(dg.enter(h));
-  const int cap = h->tuned_rk > 0 ? h->tuned_rk : 8;
-  for (int32_t c0 = 0; c0 < nrhs;) {
-    int rk = 8;
-    while (rk > 1 && (rk > cap || c0 + rk > nrhs)) rk /= 2;
-    OwnerPlan* p = nullptr;
-    while (true) {
-      const csrc_status st = owner_for(h, rk, &p);
-      if (st == CSRC_OK) break;
-      if (st != CSRC_ERR_NOT_PARTITIONED || rk == 1) return st;
-      rk /= 2;
-    }
-    const void* xc = static_cast<const char*>(X) + (size_t)c0 * h->xbytes();
-    void* yc = static_cast<char*>(Y) + (size_t)c0 * h->xbytes();
-    CSRC_TRY_S(run_owner(h, *p, transpose, xc, yc, p->spill_buf, nrhs, rk, s));
-    c0 += rk;
-  }
-  return CSRC_OK;
-}
-
 // ---------------------------------------------------------------------------- batched products
 // A batch executor. Each member runs at its own mode (storage and precision): members whose
 // strategy is the window strategy become units (member, column chunk of rk columns), whose
@@ -1014,6 +994,16 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
   std::vector<Unit> units;
   std::vector<OwnerArgs> uargs;
   std::vector<OwnerAccArgs> uacc;
+  // non-zeros per band: kOwnerBandNnz, or less when the whole batch would not fill four waves
+  // of the GPU's resident CTAs
+  int64_t total_nnz = 0;  // non-zeros of all the column chunks of all members
+  int sms = 1;
+  for (int32_t b = 0; b < batch; ++b) {
+    total_nnz += ((int64_t)hs[b]->n + 2 * hs[b]->h) * (int64_t)column_chunks(hs[b], nrhs).size();
+    sms = std::max(sms, hs[b]->sms);
+  }
+  const int64_t band_nnz =
+      std::max<int64_t>(4096, std::min<int64_t>(kOwnerBandNnz, total_nnz / ((int64_t)sms * owner_ctas_per_sm(1) * 4)));
   for (int32_t b = 0; b < batch; ++b) {
     csrc_matrix_s* h = hs[b];
     e->hs.push_back(h);
@@ -1040,7 +1030,7 @@ csrc_status build_batch(const csrc_handle* hs, int32_t batch, const void* const*
         const auto c = todo.back();
         todo.pop_back();
         OwnerPlan* p = nullptr;
-        const csrc_status st = owner_batch_for(h, c.second, &p);
+        const csrc_status st = owner_batch_for(h, c.second, band_nnz, &p);
         if (st == CSRC_OK) {
           chunks.push_back({c.first, p});
         } else if (st == CSRC_ERR_NOT_PARTITIONED && c.second > 1) {  // narrower passes fit better
@@ -1773,6 +1763,13 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
   try {
     DeviceGuard dg;
     CSRC_TRY_S(dg.enter(hs[0]));
+    if (batch == 1 && nrhs == 1) {
+      // one vector of one matrix: its own plans (bands in whole waves of the GPU), no graph
+      if (!is_device_ptr(X[0]) || !is_device_ptr(Y[0])) return CSRC_ERR_INVALID_ARG;
+      return run_spmv(hs[0], X[0], Y[0], CSRC_STRAT_AUTO, stream, transpose != 0);
+    }
+    // several columns (even of one matrix) or several matrices: every column chunk's bands are
+    // tiles of one launch per group, with one accumulation, replayed as a graph
     return run_batch(hs, batch, X, Y, nrhs, transpose != 0 ? 1 : 0, stream);
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
@@ -1901,18 +1898,15 @@ csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nr
     csrc_status st = CSRC_OK;
     for (int32_t rk = 1; rk <= 8 && st == CSRC_OK; rk *= 2) {
       if (rk > nrhs) break;
-      OwnerPlan* p = nullptr;
-      const csrc_status ps = owner_for(h, rk, &p);
-      if (ps == CSRC_ERR_NOT_PARTITIONED) break;  // wider passes fit even less
-      if (ps != CSRC_OK) {
-        st = ps;
-        break;
-      }
       h->tuned_rk = rk;
-      if ((st = spmm_one(h, X, Y, nrhs, false, stream)) != CSRC_OK) break;  // warm-up
+      ++h->generation;
+      const csrc_handle one[1] = {h};
+      const void* const xs1[1] = {X};
+      void* const ys1[1] = {Y};
+      if ((st = run_batch(one, 1, xs1, ys1, nrhs, 0, stream)) != CSRC_OK) break;  // warm-up
       float ms = 0.f;
       cudaError_t ce = cudaEventRecord(e0, stream);
-      for (int i = 0; i < 3 && st == CSRC_OK && ce == cudaSuccess; ++i) st = spmm_one(h, X, Y, nrhs, false, stream);
+      for (int i = 0; i < 3 && st == CSRC_OK && ce == cudaSuccess; ++i) st = run_batch(one, 1, xs1, ys1, nrhs, 0, stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(e1, stream);
       if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
       if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);

@@ -185,8 +185,10 @@ inline int owner_acc_bytes(int mode) { return mode == OM_F64 ? 8 : 4; }   // win
 inline int owner_vec_bytes(int mode) { return (mode == OM_F64 || mode >= OM_F32_X64) ? 8 : 4; }  // x, y
 
 // Kernel shape: threads per CTA and CTAs per SM the window budget is sized for.
-constexpr int kOwnerThreads = 256;
-inline int owner_ctas_per_sm(int rk) { return rk <= 1 ? 4 : (rk <= 2 ? 2 : 1); }
+// Four CTAs of 256 threads per SM for every column count: wider passes get smaller bands (a
+// window holds rk columns of x) rather than fewer warps, which measured faster for rk = 2..8.
+__host__ __device__ constexpr int owner_threads(int rk) { return rk > 0 ? 256 : 256; }
+__host__ __device__ constexpr int owner_ctas_per_sm(int rk) { return rk > 0 ? 4 : 4; }
 inline int owner_smem_budget(int rk) { return smem_limit_for(owner_ctas_per_sm(rk)); }
 
 struct OwnerPlan {

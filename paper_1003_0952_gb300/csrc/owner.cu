@@ -5,7 +5,7 @@
 namespace csrc {
 
 template <int MODE, int RK>
-__global__ void __launch_bounds__(kOwnerThreads, (RK <= 1 ? 4 : (RK <= 2 ? 2 : 1))) owner_kernel(OwnerArgs a) {
+__global__ void __launch_bounds__(owner_threads(RK), owner_ctas_per_sm(RK)) owner_kernel(OwnerArgs a) {
   owner_body<MODE, RK>(a, blockIdx.x + a.band_offset);
 }
 
@@ -192,10 +192,10 @@ cudaError_t prepare_owner_kernels() {
 template <int MODE>
 static void launch_owner_mode(int rk, const OwnerArgs& a, dim3 grid, int smem, cudaStream_t s) {
   switch (rk) {
-    case 1: owner_kernel<MODE, 1><<<grid, kOwnerThreads, smem, s>>>(a); break;
-    case 2: owner_kernel<MODE, 2><<<grid, kOwnerThreads, smem, s>>>(a); break;
-    case 4: owner_kernel<MODE, 4><<<grid, kOwnerThreads, smem, s>>>(a); break;
-    default: owner_kernel<MODE, 8><<<grid, kOwnerThreads, smem, s>>>(a); break;
+    case 1: owner_kernel<MODE, 1><<<grid, owner_threads(1), smem, s>>>(a); break;
+    case 2: owner_kernel<MODE, 2><<<grid, owner_threads(2), smem, s>>>(a); break;
+    case 4: owner_kernel<MODE, 4><<<grid, owner_threads(4), smem, s>>>(a); break;
+    default: owner_kernel<MODE, 8><<<grid, owner_threads(8), smem, s>>>(a); break;
   }
 }
 

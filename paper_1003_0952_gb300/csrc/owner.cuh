@@ -73,6 +73,27 @@ __device__ __forceinline__ double owner_ldv(const double* p) { return __ldg(p); 
 __device__ __forceinline__ float owner_ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ uint16_t owner_ldv(const uint16_t* p) { return __ldg(p); }
 
+// The RK columns of x of window slot s, with 16-byte shared-memory loads where they fit.
+template <typename A, int RK>
+__device__ __forceinline__ void owner_window_x(const A* xs, uint32_t s, A (&xv)[RK]) {
+  constexpr int kVec = 16 / (int)sizeof(A);  // elements per 16-byte load
+  if constexpr (RK % kVec == 0) {
+    const uint4* p = reinterpret_cast<const uint4*>(xs + (size_t)s * RK);
+#pragma unroll
+    for (int q = 0; q < RK / kVec; ++q) {
+      const uint4 w = p[q];
+      A t[kVec];
+      static_assert(sizeof(t) == sizeof(uint4), "16-byte vector");
+      __builtin_memcpy(t, &w, sizeof(w));
+#pragma unroll
+      for (int c = 0; c < kVec; ++c) xv[q * kVec + c] = t[c];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < RK; ++c) xv[c] = xs[(size_t)s * RK + c];
+  }
+}
+
 // Loads of steps m0 .. m0 + U - 1 of a slice for this lane (slot and value; 0 past the lane's
 // list). off is the first entry of step m0 and is advanced past the batch: step m holds one
 // entry for every lane whose list is longer than m, and those lanes come first.
@@ -98,17 +119,14 @@ __device__ __forceinline__ void owner_load_batch(const uint16_t* __restrict__ S,
 template <typename A, typename V, int U, int RK>
 __device__ __forceinline__ void owner_fma_batch(const A* xs, int m0, int len, const uint32_t (&sv)[U],
                                                 const V (&vv)[U], A (&acc)[RK]) {
-  A xv[U][RK];
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-#pragma unroll
-    for (int c = 0; c < RK; ++c) xv[u][c] = xs[sv[u] * RK + c];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
+    A xv[RK];
+    owner_window_x<A, RK>(xs, sv[u], xv);
     if (m0 + u < len) {
       const A v = owner_widen(vv[u]);
 #pragma unroll
-      for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[u][c], acc[c]);
+      for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[c], acc[c]);
     }
   }
 }
@@ -130,16 +148,22 @@ __device__ __forceinline__ void owner_load_full(const uint16_t* __restrict__ pS,
 template <typename A, typename V, int U, int RK>
 __device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)[U], const V (&vv)[U],
                                                A (&acc)[RK]) {
-  A xv[U][RK];
+  if constexpr (RK == 1) {
+    // single columns: all U window loads first, so that their latencies overlap
+    A xv[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u)
+    for (int u = 0; u < U; ++u) xv[u] = xs[sv[u]];
 #pragma unroll
-    for (int c = 0; c < RK; ++c) xv[u][c] = xs[sv[u] * RK + c];
+    for (int u = 0; u < U; ++u) acc[0] = owner_fma(owner_widen(vv[u]), xv[u], acc[0]);
+  } else {
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const A v = owner_widen(vv[u]);
+    for (int u = 0; u < U; ++u) {
+      A xv[RK];
+      owner_window_x<A, RK>(xs, sv[u], xv);
+      const A v = owner_widen(vv[u]);
 #pragma unroll
-    for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[u][c], acc[c]);
+      for (int c = 0; c < RK; ++c) acc[c] = owner_fma(v, xv[c], acc[c]);
+    }
   }
 }
 
@@ -147,7 +171,7 @@ __device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)
 // values, whose multiply-adds are too quick to hide a batch's latency on their own.
 template <int ST>
 constexpr int owner_unroll(int rk) {
-  return rk == 1 ? 4 : (rk == 2 ? 4 : 2);
+  return rk == 1 ? 4 : (ST == OM_F64 ? 4 : 6);
 }
 
 // Band b of the product described by a, run by the whole CTA.

@@ -7,7 +7,7 @@
 namespace csrc {
 
 template <int MODE, int RK>
-__global__ void __launch_bounds__(kOwnerThreads, (RK <= 1 ? 4 : (RK <= 2 ? 2 : 1)))
+__global__ void __launch_bounds__(owner_threads(RK), owner_ctas_per_sm(RK))
     owner_batch_kernel(const OwnerArgs* __restrict__ members, const OwnerTile* __restrict__ tiles) {
   const OwnerTile t = tiles[blockIdx.x];
   OwnerArgs a = members[t.member];
@@ -45,10 +45,10 @@ template <int MODE>
 static void launch_batch_mode(int rk, const OwnerArgs* members, const OwnerTile* tiles, dim3 grid, int smem,
                               cudaStream_t s) {
   switch (rk) {
-    case 1: owner_batch_kernel<MODE, 1><<<grid, kOwnerThreads, smem, s>>>(members, tiles); break;
-    case 2: owner_batch_kernel<MODE, 2><<<grid, kOwnerThreads, smem, s>>>(members, tiles); break;
-    case 4: owner_batch_kernel<MODE, 4><<<grid, kOwnerThreads, smem, s>>>(members, tiles); break;
-    default: owner_batch_kernel<MODE, 8><<<grid, kOwnerThreads, smem, s>>>(members, tiles); break;
+    case 1: owner_batch_kernel<MODE, 1><<<grid, owner_threads(1), smem, s>>>(members, tiles); break;
+    case 2: owner_batch_kernel<MODE, 2><<<grid, owner_threads(2), smem, s>>>(members, tiles); break;
+    case 4: owner_batch_kernel<MODE, 4><<<grid, owner_threads(4), smem, s>>>(members, tiles); break;
+    default: owner_batch_kernel<MODE, 8><<<grid, owner_threads(8), smem, s>>>(members, tiles); break;
   }
 }
 
