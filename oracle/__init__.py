@@ -94,6 +94,8 @@ def _load():
             lib.oracle_priority_order.argtypes = [ctypes.c_int64, ctypes.c_uint64, I64P]
             lib.oracle_greedy_color.restype = ctypes.c_int64
             lib.oracle_greedy_color.argtypes = [ctypes.c_int64, I64P, I32P, I64P, I32P]
+            lib.oracle_greedy_color_stride.restype = ctypes.c_int64
+            lib.oracle_greedy_color_stride.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int64, I32P]
             lib.oracle_check_coloring.restype = ctypes.c_int
             lib.oracle_check_coloring.argtypes = [ctypes.c_int64, I64P, I32P, I32P, ctypes.c_int64]
             _lib = lib
@@ -447,6 +449,31 @@ def greedy_color(c: CSRC, order) -> tuple[int, np.ndarray]:
     if k < 0:
         raise MemoryError
     return int(k), colors[:c.n]
+
+
+def greedy_color_stride(c: CSRC, stride: int) -> tuple[int, np.ndarray]:
+    """Stride-bounded greedy colouring (the future work of Section 6), in ascending row order:
+    first fit among the colours without a conflict whose last member lies at most `stride`
+    rows back; stride <= 0 means no bound."""
+    lib = _load()
+    ia, ja = _i64(c.ia), _i32(c.ja)
+    colors = np.empty(max(c.n, 1), np.int32)
+    k = lib.oracle_greedy_color_stride(c.n, _p(ia, I64P), _p(ja if len(ja) else np.zeros(1, np.int32), I32P),
+                                       int(stride), _p(colors, I32P))
+    if k < 0:
+        raise MemoryError
+    return int(k), colors[:c.n]
+
+
+def max_class_gap(colors, ncolors: int) -> int:
+    """Largest distance between consecutive rows of one colour class (0 for classes of one row)."""
+    colors = np.asarray(colors)
+    worst = 0
+    for k in range(ncolors):
+        rows = np.nonzero(colors == k)[0]
+        if len(rows) > 1:
+            worst = max(worst, int(np.diff(rows).max()))
+    return worst
 
 
 def jp_color(c: CSRC, seed: int) -> tuple[int, np.ndarray]:

@@ -352,6 +352,42 @@ int64_t oracle_greedy_color(int64_t n, const int64_t* ia, const int32_t* ja, con
   return ncolors;
 }
 
+/* Stride-bounded greedy colouring (the future work named in Section 6: a maximum stride
+ * inside each colour class), in this reading: rows are coloured in ascending order, the
+ * sequential greedy colouring of Section 3.2 in the matrix's own order, and row u takes
+ * the smallest colour c that no earlier row writing into W(u) holds and whose last member
+ * lies at most `stride` rows before u; when no colour qualifies a new one is opened. With
+ * stride <= 0 there is no bound (plain greedy in ascending order). Returns the number of
+ * colours, -1 on allocation failure. */
+int64_t oracle_greedy_color_stride(int64_t n, const int64_t* ia, const int32_t* ja, int64_t stride,
+                                   int32_t* colors) {
+  int64_t *up_ptr, *up;
+  if (build_upper(n, ia, ja, &up_ptr, &up)) return -1;
+  int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1)); /* mark[c] = row that saw colour c */
+  int64_t* last = (int64_t*)malloc(sizeof(int64_t) * ((size_t)n + 1)); /* last member of colour c */
+  if (!mark || !last) { free(mark); free(last); free(up_ptr); free(up); return -1; }
+  for (int64_t c = 0; c <= n; ++c) { mark[c] = -1; last[c] = -1; }
+  for (int64_t i = 0; i < n; ++i) colors[i] = -1;
+  int64_t ncolors = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t q = ia[u] - 1; q < ia[u + 1]; ++q) {
+      int64_t t = (q < ia[u]) ? u : ja[q];
+      if (t != u && colors[t] >= 0) mark[colors[t]] = u;
+      for (int64_t p = up_ptr[t]; p < up_ptr[t + 1]; ++p) {
+        int64_t v = up[p];
+        if (v != u && colors[v] >= 0) mark[colors[v]] = u;
+      }
+    }
+    int64_t c = 0;
+    while (c < ncolors && (mark[c] == u || (stride > 0 && u - last[c] > stride))) ++c;
+    colors[u] = (int32_t)c;
+    last[c] = u;
+    if (c + 1 > ncolors) ncolors = c + 1;
+  }
+  free(mark); free(last); free(up_ptr); free(up);
+  return ncolors;
+}
+
 /* Validity of a colouring: within each colour class the write sets W(i) are
  * pairwise disjoint. Returns 0 if valid, 1 if two rows of one colour write the
  * same y entry, 2 if a colour is out of [0, ncolors), -1 on allocation failure. */

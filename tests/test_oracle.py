@@ -631,3 +631,85 @@ def test_config_sizes():
     assert small.n == 375 and small.nnz == 9 * rp5[-1]
     cc = oracle.from_matrix(small)
     assert cc.pairs == (small.nnz - small.n) // 2
+
+
+# --------------------------------------------------------------------------- stride-bounded colouring
+def _write_sets(c):
+    """W(i) = {i} U ja(row i): the y entries row i writes (Section 3.2 conflicts)."""
+    return [{i} | {int(j) for j in c.ja[c.ia[i]:c.ia[i + 1]]} for i in range(c.n)]
+
+
+def _stride_greedy_brute_force(c, stride):
+    """The stride-bounded reading written out directly: ascending rows, first fit among the
+    colours whose members never share a written y entry with the row and whose last member is
+    at most `stride` rows back (no bound for stride <= 0); a new colour otherwise."""
+    W = _write_sets(c)
+    classes = []  # list of member lists, ascending
+    colors = [-1] * c.n
+    for i in range(c.n):
+        chosen = None
+        for k, members in enumerate(classes):
+            if any(W[i] & W[r] for r in members):
+                continue
+            if stride > 0 and i - members[-1] > stride:
+                continue
+            chosen = k
+            break
+        if chosen is None:
+            classes.append([])
+            chosen = len(classes) - 1
+        classes[chosen].append(i)
+        colors[i] = chosen
+    return len(classes), np.array(colors, np.int32)
+
+
+@pytest.mark.parametrize("n,density,seed", SMALL + [(120, 0.05, 10), (200, 0.02, 11)])
+@pytest.mark.parametrize("stride", [0, 1, 3, 8, 40])
+def test_stride_colouring_matches_brute_force(n, density, seed, stride):
+    c = oracle.from_matrix(_random_matrix(n, density, seed))
+    k, colors = oracle.greedy_color_stride(c, stride)
+    k_ref, colors_ref = _stride_greedy_brute_force(c, stride)
+    assert k == k_ref
+    np.testing.assert_array_equal(colors, colors_ref)
+
+
+@pytest.mark.parametrize("stride", [1, 2, 16, 64, 500])
+def test_stride_colouring_invariants_on_meshes(stride):
+    for m in (fe.p1_grid(30, 20, 3), fe.q1_hex(7, 3, 4), fe.tet_mesh(1500, 5, method="kuhn")):
+        c = oracle.from_matrix(m)
+        k, colors = oracle.greedy_color_stride(c, stride)
+        assert oracle.check_coloring(c, colors, k) == 0  # valid: no two rows of a class conflict
+        assert oracle.max_class_gap(colors, k) <= stride  # the stride bound inside every class
+
+
+def test_unbounded_stride_is_ascending_greedy():
+    # stride <= 0: plain sequential greedy colouring in the matrix's own order (Section 3.2)
+    for m in (fe.p1_grid(25, 19, 6), fe.q1_hex(6, 3, 7), _random_matrix(300, 0.03, 8)):
+        c = oracle.from_matrix(m)
+        k, colors = oracle.greedy_color_stride(c, 0)
+        k2, colors2 = oracle.greedy_color(c, np.arange(m.n))
+        assert k == k2
+        np.testing.assert_array_equal(colors, colors2)
+        # and a stride as long as the matrix binds nothing
+        k3, colors3 = oracle.greedy_color_stride(c, m.n)
+        np.testing.assert_array_equal(colors3, colors)
+
+
+def test_stride_of_one_forces_consecutive_members():
+    # stride 1: a class is a run of consecutive rows that pairwise do not conflict; on a
+    # tridiagonal pattern every row conflicts with its neighbour, so every class is one row
+    # until the class of row i - 2 can no longer be reached
+    n = 12
+    ei, ej = np.arange(1, n), np.arange(0, n - 1)
+    rp, col = fe.pattern_from_edges(n, ei, ej)
+    c = oracle.from_matrix(fe.FEMatrix(n, rp, col, np.ones(len(col))))
+    k, colors = oracle.greedy_color_stride(c, 1)
+    assert k == n
+    assert oracle.max_class_gap(colors, k) == 0
+
+
+def test_class_gap_checker_detects_a_planted_violation():
+    colors = np.array([0, 1, 0, 1, 1, 0, 2], np.int32)  # class 0: rows 0, 2, 5 -> gap 3
+    assert oracle.max_class_gap(colors, 3) == 3
+    colors[5] = 1  # class 0: rows 0, 2 -> gap 2; class 1: rows 1, 3, 4, 5 -> gap 2
+    assert oracle.max_class_gap(colors, 3) == 2
