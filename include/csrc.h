@@ -77,7 +77,8 @@ typedef enum {
                             when the plan is built: every window row is summed by one lane, with no
                             atomics; rows below a band are folded in by a deterministic accumulation
                             kernel. Bitwise reproducible from run to run. */
-  CSRC_STRAT_COLOR = 2,  /* colour-ordered rows, no atomics (needs csrc_color()) */
+  CSRC_STRAT_COLOR = 2,  /* colour-ordered rows, no atomics (needs csrc_color() or csrc_color_stride()):
+                            every class in one cooperative launch with a bounded grid barrier */
   CSRC_STRAT_ATOMIC = 3, /* stream-order windows flushed with global FP64/FP32 atomic adds */
   CSRC_STRAT_WINDOW_ATOMIC = 4 /* stream-order windows: each pair scatters into the shared-memory window
                                   with an atomic add as it streams past, rows below a band go through the
@@ -220,6 +221,20 @@ csrc_status csrc_partition(csrc_handle h, int32_t nbands, int32_t* band_ptr_out)
  * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA, DEVICE_TIMEOUT (a round limit ran out).
  */
 csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32_t* colors_out);
+
+/*
+ * Stride-bounded colouring (the future work named in Section 6: "fixing the maximum allowed
+ * stride size inside each color class"), in this reading: rows are coloured in ascending
+ * order (the sequential greedy colouring of Section 3.2 in the matrix's own order, which keeps
+ * the locality of its reordering), and row i takes the smallest colour c that no earlier row
+ * writing into W(i) holds and whose last member lies at most `stride` rows before i; when no
+ * colour qualifies a new one is opened. Every class therefore visits its rows with gaps of at
+ * most `stride`. stride <= 0 means no bound. Runs on the host (it is sequential by
+ * definition); the classes replace any earlier colouring of the handle. Synchronous.
+ *   ncolors_out, colors_out  as for csrc_color
+ * Errors: INVALID_ARG (more than 65536 colours), OUT_OF_MEMORY, CUDA.
+ */
+csrc_status csrc_color_stride(csrc_handle h, int64_t stride, int32_t* ncolors_out, int32_t* colors_out);
 
 /* y = A x (Fig. 2(a)) with the given strategy. Asynchronous on stream. */
 csrc_status csrc_spmv(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream);

@@ -108,6 +108,7 @@ SIGNATURES = {
     "csrc_bicg": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int32, ctypes.c_int, _P(ctypes.c_int32),
                                  _P(ctypes.c_double), _VP]),
     "csrc_color": (ctypes.c_int, [_VP, ctypes.c_uint64, _P(ctypes.c_int32), _VP]),
+    "csrc_color_stride": (ctypes.c_int, [_VP, ctypes.c_int64, _P(ctypes.c_int32), _VP]),
     "csrc_spmv": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "csrc_spmv_t": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP]),
     "csrc_spmm_batched": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(_VP), _P(_VP), ctypes.c_int32, ctypes.c_int32,
@@ -231,6 +232,13 @@ def csrc_color(h, seed, colors_out=None) -> int:
     nc = ctypes.c_int32(0)
     _check(_lib.csrc_color(h, ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), ctypes.byref(nc), _ptr(colors_out)),
            "csrc_color")
+    return nc.value
+
+
+def csrc_color_stride(h, stride, colors_out=None) -> int:
+    """Stride-bounded colouring (ascending rows, class gaps of at most stride; 0 = unbounded)."""
+    nc = ctypes.c_int32(0)
+    _check(_lib.csrc_color_stride(h, int(stride), ctypes.byref(nc), _ptr(colors_out)), "csrc_color_stride")
     return nc.value
 
 

@@ -91,6 +91,8 @@ struct csrc_matrix_s {
   // colouring
   int32_t ncolors = 0;
   int32_t* d_color_rows = nullptr;
+  int32_t* d_color_ptr = nullptr;  // device copy of color_ptr
+  unsigned* d_barrier = nullptr;   // grid barrier counter of the colour product
   std::vector<int32_t> color_ptr;
   // staging for host vectors
   void* d_xs = nullptr;
@@ -865,13 +867,12 @@ csrc_status run_spmv(csrc_matrix_s* h, const void* x, void* y, csrc_strategy st,
     CSRC_TRY_S(run_owner(h, *op, transpose, dx, dy, op->spill_buf, 1, 1, s));
   } else if (strat == CSRC_STRAT_COLOR) {
     CSRC_TRY(cudaMemsetAsync(dy, 0, vb, s));
-    for (int32_t c = 0; c < h->ncolors; ++c) {
-      const int32_t a = h->color_ptr[c], b = h->color_ptr[c + 1];
-      CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s, [&] {
-        return launch_color_spmv(h->arith, h->storage, b - a, h->d_color_rows + a, h->d_ia, h->d_ja, g, sc, h->d_ad,
-                                 dx, dy, s);
-      }));
-    }
+    CSRC_TRY(cudaMemsetAsync(h->d_barrier, 0, sizeof(unsigned), s));
+    const int group = color_group(h->n > 0 ? (double)h->h / (double)h->n : 0.0);
+    CSRC_TRY(timed_launch(h, CSRC_KERNEL_PRODUCT, s, [&] {
+      return launch_color_spmv(h->storage, group, h->ncolors, h->d_color_ptr, h->d_color_rows, h->d_ia, h->d_ja, g,
+                               sc, h->d_ad, dx, dy, h->d_barrier, h->d_status, s);
+    }));
   } else {
     const bool atomic = strat == CSRC_STRAT_ATOMIC;
     DevPlan* p = &h->plan;  // the atomic strategy runs plain rows
@@ -1415,6 +1416,38 @@ csrc_status create_from_host_csr(csrc_handle* out, int32_t n, const int64_t* row
   return CSRC_OK;
 }
 
+// Install a colouring (colour of every row) as the handle's colour classes: rows grouped by
+// colour, ascending within a class, on the device with the class pointers.
+csrc_status set_colouring(csrc_matrix_s* h, const std::vector<int32_t>& color, int32_t* ncolors_out,
+                          int32_t* colors_out) {
+  const int32_t n = h->n;
+  int32_t nc = 0;
+  for (int32_t v : color) nc = std::max(nc, v + 1);
+  std::vector<int32_t> cptr((size_t)nc + 1, 0), rows((size_t)std::max(n, 1));
+  for (int32_t i = 0; i < n; ++i) cptr[(size_t)color[(size_t)i] + 1]++;
+  for (int32_t c = 0; c < nc; ++c) cptr[(size_t)c + 1] += cptr[(size_t)c];
+  {
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int32_t i = 0; i < n; ++i) rows[(size_t)fill[(size_t)color[(size_t)i]]++] = i;
+  }
+  cudaStream_t s = 0;
+  dfree(h->d_color_rows);
+  dfree(h->d_color_ptr);
+  h->d_color_rows = nullptr;
+  h->d_color_ptr = nullptr;
+  h->ncolors = 0;
+  CSRC_TRY(upload(&h->d_color_rows, rows, s));
+  CSRC_TRY(upload(&h->d_color_ptr, cptr, s));
+  if (!h->d_barrier) CSRC_TRY(dmalloc(&h->d_barrier, 1));
+  CSRC_TRY(cudaStreamSynchronize(s));
+  h->color_ptr.swap(cptr);
+  h->ncolors = nc;
+  ++h->generation;
+  if (ncolors_out) *ncolors_out = nc;
+  if (colors_out) std::copy(color.begin(), color.end(), colors_out);
+  return CSRC_OK;
+}
+
 }  // namespace
 
 namespace csrc {
@@ -1710,27 +1743,58 @@ csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32
     if (e == cudaSuccess) e = cudaMemcpy(state.data(), d_state, (size_t)n * 4, cudaMemcpyDeviceToHost);
     cleanup();
     if (e != cudaSuccess) return from_cuda(e);
-    int32_t nc = 0;
-    for (auto& v : state) {
-      v &= 0xffff;
-      nc = std::max(nc, v + 1);
-    }
-    std::vector<int32_t> cptr((size_t)nc + 1, 0), rows((size_t)n);
-    for (int32_t i = 0; i < n; ++i) cptr[(size_t)state[i] + 1]++;
-    for (int32_t c = 0; c < nc; ++c) cptr[c + 1] += cptr[c];
+    for (auto& v : state) v &= 0xffff;
+    return set_colouring(h, state, ncolors_out, colors_out);
+  } catch (const std::bad_alloc&) {
+    return CSRC_ERR_OUT_OF_MEMORY;
+  }
+}
+
+csrc_status csrc_color_stride(csrc_handle h, int64_t stride, int32_t* ncolors_out, int32_t* colors_out) {
+  if (!h) return CSRC_ERR_INVALID_ARG;
+  DeviceGuard dg;
+  CSRC_TRY_S(dg.enter(h));
+  const int32_t n = h->n;
+  try {
+    // rows of A_U's columns: the rows v > t with t in their ja, ascending
+    std::vector<int32_t> up_ptr((size_t)n + 1, 0);
+    for (int32_t t : h->ja) up_ptr[(size_t)t + 1]++;
+    for (int32_t t = 0; t < n; ++t) up_ptr[(size_t)t + 1] += up_ptr[(size_t)t];
+    std::vector<int32_t> up(h->ja.size());
     {
-      std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
-      for (int32_t i = 0; i < n; ++i) rows[(size_t)fill[state[i]]++] = i;
+      std::vector<int32_t> fill(up_ptr.begin(), up_ptr.end() - 1);
+      for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = h->ia[(size_t)v]; k < h->ia[(size_t)v + 1]; ++k) up[(size_t)fill[(size_t)h->ja[(size_t)k]]++] = v;
     }
-    dfree(h->d_color_rows);
-    h->d_color_rows = nullptr;
-    CSRC_TRY(upload(&h->d_color_rows, rows, s));
-    CSRC_TRY(cudaStreamSynchronize(s));
-    h->color_ptr.swap(cptr);
-    h->ncolors = nc;
-    if (ncolors_out) *ncolors_out = nc;
-    if (colors_out) std::copy(state.begin(), state.end(), colors_out);
-    return CSRC_OK;
+    // rows in ascending order; banned[c] == i marks colour c as held by an earlier row that
+    // writes into W(i); last[c] is colour c's latest member
+    std::vector<int32_t> color((size_t)n, -1), banned, last;
+    for (int32_t i = 0; i < n; ++i) {
+      auto ban = [&](int32_t v) {
+        if (v < i) banned[(size_t)color[(size_t)v]] = i;  // rows below i are coloured already
+      };
+      const int32_t k0 = h->ia[(size_t)i], k1 = h->ia[(size_t)i + 1];
+      for (int32_t q = k0 - 1; q < k1; ++q) {
+        const int32_t t = q < k0 ? i : h->ja[(size_t)q];
+        if (t != i) ban(t);
+        for (int32_t p = up_ptr[(size_t)t]; p < up_ptr[(size_t)t + 1]; ++p) {
+          const int32_t v = up[(size_t)p];
+          if (v >= i) break;  // ascending: the rest are not coloured yet
+          ban(v);
+        }
+      }
+      int32_t c = 0;
+      const int32_t nc = (int32_t)last.size();
+      while (c < nc && (banned[(size_t)c] == i || (stride > 0 && (int64_t)i - last[(size_t)c] > stride))) ++c;
+      if (c == nc) {
+        if (nc >= 65536) return CSRC_ERR_INVALID_ARG;  // more than 65536 colours
+        last.push_back(i);
+        banned.push_back(-1);
+      }
+      color[(size_t)i] = c;
+      last[(size_t)c] = i;
+    }
+    return set_colouring(h, color, ncolors_out, colors_out);
   } catch (const std::bad_alloc&) {
     return CSRC_ERR_OUT_OF_MEMORY;
   }
@@ -2218,7 +2282,8 @@ csrc_status csrc_destroy(csrc_handle h) {
   dfree(h->d_rrow); dfree(h->d_rptr); dfree(h->d_rcol); dfree(h->d_rval);
   dfree(h->d_tptr); dfree(h->d_trow); dfree(h->d_tval);
   dfree(h->d_solve); dfree(h->d_partial);
-  dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_xs); dfree(h->d_ys);
+  dfree(h->d_status); dfree(h->d_color_rows); dfree(h->d_color_ptr); dfree(h->d_barrier); dfree(h->d_xs);
+  dfree(h->d_ys);
   release_timing(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   delete h;

@@ -96,9 +96,13 @@ cudaError_t launch_jp_round(int32_t n, const int32_t* ia, const int32_t* ja, con
 }
 
 // ---------------------------------------------------------------------------- colour-ordered product
-// One colour class per launch, one thread per row. y was zeroed. Rows of one colour
-// write disjoint entries of y, so plain read-modify-write updates are race-free.
-// FP64 storage uses FP64-pipe arithmetic here, FP32/BF16 storage uses FP32.
+// All colour classes in one persistent, cooperative launch (every CTA resident): class c's
+// rows are spread over groups of G lanes grid-wide, then a grid barrier, then class c + 1.
+// y was zeroed. Rows of one class write disjoint entries of y, so plain read-modify-write
+// updates are race-free; they go through L2 (ld.global.cg / st.global.cg) so that the next
+// class, run by other CTAs after the barrier, sees them. A group streams its row's ja / al /
+// au slices with G lanes side by side (coalesced) and sums the row's gather with shuffles.
+// FP64 storage computes in FP64, FP32 / BF16 storage in FP32.
 template <typename V, typename X>
 __device__ __forceinline__ X to_x(V v);
 template <>
@@ -108,45 +112,147 @@ __device__ __forceinline__ float to_x<float, float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_x<uint16_t, float>(uint16_t v) { return __uint_as_float((unsigned)v << 16); }
 
-template <typename V, typename X>
-__global__ void color_rows_kernel(int32_t nrows, const int32_t* __restrict__ rows, const int32_t* __restrict__ ia,
-                                  const int32_t* __restrict__ ja, const V* __restrict__ al, const V* __restrict__ au,
-                                  const V* __restrict__ ad, const X* __restrict__ x, X* y) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nrows) return;
-  const int i = rows[t];
-  const X xi = x[i];
-  X s = to_x<V, X>(ad[i]) * xi;
-  const int k1 = ia[i + 1];
-  for (int k = ia[i]; k < k1; ++k) {
-    const int j = ja[k];
-    s = fma(to_x<V, X>(al[k]), x[j], s);
-    y[j] = fma(to_x<V, X>(au[k]), xi, y[j]);
+// Grid barrier of a cooperative launch: every CTA adds one to *bar and waits, with a bound of
+// about two seconds of SM clock, until it reaches target. Returns false when the wait ran out.
+__device__ __forceinline__ bool color_grid_sync(unsigned* bar, unsigned target) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    const long long t0 = clock64();
+    bool good = true;
+    while (atomicAdd(bar, 0u) < target) {
+      if (clock64() - t0 > 4000000000LL) {
+        good = false;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok = good ? 1 : 0;
   }
-  y[i] += s;
+  __syncthreads();
+  return ok != 0;
 }
 
-cudaError_t launch_color_spmv(Arith arith, int storage, int32_t nrows, const int32_t* rows, const int32_t* ia,
-                              const int32_t* ja, const void* al, const void* au, const void* ad, const void* x, void* y,
-                              cudaStream_t s) {
-  (void)arith;
-  if (nrows <= 0) return cudaSuccess;
-  const int bs = 128;
-  const int grid = (nrows + bs - 1) / bs;
-  if (storage == CSRC_F64) {
-    color_rows_kernel<double, double><<<grid, bs, 0, s>>>(
-        nrows, rows, ia, ja, static_cast<const double*>(al), static_cast<const double*>(au),
-        static_cast<const double*>(ad), static_cast<const double*>(x), static_cast<double*>(y));
-  } else if (storage == CSRC_F32) {
-    color_rows_kernel<float, float><<<grid, bs, 0, s>>>(
-        nrows, rows, ia, ja, static_cast<const float*>(al), static_cast<const float*>(au),
-        static_cast<const float*>(ad), static_cast<const float*>(x), static_cast<float*>(y));
-  } else {
-    color_rows_kernel<uint16_t, float><<<grid, bs, 0, s>>>(
-        nrows, rows, ia, ja, static_cast<const uint16_t*>(al), static_cast<const uint16_t*>(au),
-        static_cast<const uint16_t*>(ad), static_cast<const float*>(x), static_cast<float*>(y));
+// Threads per CTA of the colour product.
+constexpr int kColorThreads = 256;
+
+struct ColorArgs {
+  int32_t ncolors;
+  const int32_t* color_ptr;  // ncolors + 1: rows of class c are rows[color_ptr[c] .. color_ptr[c+1])
+  const int32_t* rows;
+  const int32_t* ia;
+  const int32_t* ja;
+  const void* al;  // gathered values (au for the transpose)
+  const void* au;  // scattered values
+  const void* ad;
+  const void* x;
+  void* y;
+  unsigned* barrier;  // zero at launch
+  int32_t* status;
+};
+
+template <typename V, typename X, int G>
+__global__ void __launch_bounds__(kColorThreads) color_persistent_kernel(ColorArgs a) {
+  const V* __restrict__ al = static_cast<const V*>(a.al);
+  const V* __restrict__ au = static_cast<const V*>(a.au);
+  const V* __restrict__ ad = static_cast<const V*>(a.ad);
+  const X* __restrict__ x = static_cast<const X*>(a.x);
+  X* y = static_cast<X*>(a.y);
+  const int gpb = blockDim.x / G;
+  const int ngroups = gridDim.x * gpb;
+  const int gid = blockIdx.x * gpb + threadIdx.x / G;
+  const int gl = threadIdx.x % G;
+  const int lane = threadIdx.x & 31;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  for (int c = 0; c < a.ncolors; ++c) {
+    const int p1 = __ldg(a.color_ptr + c + 1);
+    for (int idx = __ldg(a.color_ptr + c) + gid; idx < p1; idx += ngroups) {
+      const int i = __ldg(a.rows + idx);
+      const X xi = __ldg(x + i);
+      X s = X(0);
+      const int k1 = __ldg(a.ia + i + 1);
+      // four pairs per lane at a time: their loads (slices, x and y through L2) overlap
+      constexpr int U = 4;
+      for (int k0 = __ldg(a.ia + i) + gl; k0 < k1; k0 += U * G) {
+        int j[U];
+        V g[U], v[U];
+        X xj[U], yj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u * G;
+          j[u] = k < k1 ? __ldg(a.ja + k) : -1;
+          g[u] = k < k1 ? __ldg(al + k) : V(0);
+          v[u] = k < k1 ? __ldg(au + k) : V(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          xj[u] = j[u] >= 0 ? __ldg(x + j[u]) : X(0);
+          yj[u] = j[u] >= 0 ? __ldcg(y + j[u]) : X(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (j[u] >= 0) {
+            s = fma(to_x<V, X>(g[u]), xj[u], s);
+            __stcg(y + j[u], fma(to_x<V, X>(v[u]), xi, yj[u]));
+          }
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
+      if (gl == 0) {
+        X* yp = y + i;
+        __stcg(yp, __ldcg(yp) + fma(to_x<V, X>(__ldg(ad + i)), xi, s));
+      }
+    }
+    if (c + 1 < a.ncolors && !color_grid_sync(a.barrier, (unsigned)(c + 1) * gridDim.x)) {
+      if (threadIdx.x == 0) atomicOr(a.status, DEV_TIMEOUT);
+      return;
+    }
   }
-  return cudaGetLastError();
+}
+
+// Lanes per row: about a quarter of the mean row length, a power of two in [1, 32] (measured
+// against an eighth and a sixteenth on the Q1 matrices: 4 lanes for q1s_96, 16 for q1v_96).
+int color_group(double mean_pairs) {
+  int g = 1;
+  while (g < 32 && 4.0 * g < mean_pairs) g *= 2;
+  return g;
+}
+
+template <typename V, typename X>
+static cudaError_t launch_color_typed(int group, const ColorArgs& a, cudaStream_t s) {
+  void* fn = nullptr;
+  switch (group) {
+    case 1: fn = (void*)color_persistent_kernel<V, X, 1>; break;
+    case 2: fn = (void*)color_persistent_kernel<V, X, 2>; break;
+    case 4: fn = (void*)color_persistent_kernel<V, X, 4>; break;
+    case 8: fn = (void*)color_persistent_kernel<V, X, 8>; break;
+    case 16: fn = (void*)color_persistent_kernel<V, X, 16>; break;
+    default: fn = (void*)color_persistent_kernel<V, X, 32>; break;
+  }
+  int dev = 0, sms = 1, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kColorThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm <= 0) return cudaErrorLaunchOutOfResources;
+  const int grid = sms * per_sm;  // every CTA resident at once: the grid barrier needs it
+  ColorArgs args = a;
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kColorThreads), params, 0, s);
+}
+
+cudaError_t launch_color_spmv(int storage, int group, int32_t ncolors, const int32_t* color_ptr, const int32_t* rows,
+                              const int32_t* ia, const int32_t* ja, const void* al, const void* au, const void* ad,
+                              const void* x, void* y, unsigned* barrier, int32_t* status, cudaStream_t s) {
+  if (ncolors <= 0) return cudaSuccess;
+  ColorArgs a{ncolors, color_ptr, rows, ia, ja, al, au, ad, x, y, barrier, status};
+  if (storage == CSRC_F64) return launch_color_typed<double, double>(group, a, s);
+  if (storage == CSRC_F32) return launch_color_typed<float, float>(group, a, s);
+  return launch_color_typed<uint16_t, float>(group, a, s);
 }
 
 }  // namespace csrc

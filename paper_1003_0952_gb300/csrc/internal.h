@@ -374,8 +374,12 @@ csrc_status spmv_external_spill(csrc_matrix_s* h, const void* x, void* y, bool t
 cudaError_t launch_jp_round(int32_t n, const int32_t* ia, const int32_t* ja, const int32_t* up_ptr,
                             const int32_t* up, uint64_t seed, int32_t round, int32_t* state,
                             int32_t* uncolored, cudaStream_t s);
-cudaError_t launch_color_spmv(Arith arith, int storage, int32_t nrows, const int32_t* rows, const int32_t* ia,
-                              const int32_t* ja, const void* al, const void* au, const void* ad, const void* x,
-                              void* y, cudaStream_t s);
+// Colour-ordered product (color.cu): every class in one cooperative launch with grid barriers
+// (barrier: a zeroed counter), `group` lanes per row. A barrier wait that runs out sets
+// DEV_TIMEOUT in *status.
+int color_group(double mean_pairs);
+cudaError_t launch_color_spmv(int storage, int group, int32_t ncolors, const int32_t* color_ptr, const int32_t* rows,
+                              const int32_t* ia, const int32_t* ja, const void* al, const void* au, const void* ad,
+                              const void* x, void* y, unsigned* barrier, int32_t* status, cudaStream_t s);
 
 }  // namespace csrc

@@ -597,3 +597,45 @@ def test_scalar_matrix_has_no_node_blocks(cs):
         assert cs.csrc_get_info(h.h)["block"] == 1
     finally:
         h.close()
+
+
+# --------------------------------------------------------------------------- stride-bounded colouring
+@pytest.mark.parametrize("stride", [0, 1, 7, 64, 1000])
+def test_stride_colouring_matches_oracle(cs, stride):
+    # the library's host colouring (ascending rows, class gaps <= stride) equals the oracle's
+    # bit for bit, is valid, and the colour product on its classes matches the oracle
+    for m in (fe.p1_grid(40, 25, 3), fe.q1_hex(8, 3, 4), fe.tet_mesh(4000, 6, method="kuhn")):
+        c = oracle.from_matrix(m)
+        h = Handle(cs, m)
+        try:
+            colors = np.zeros(m.n, np.int32)
+            k = cs.csrc_color_stride(h.h, stride, colors)
+            k_ref, colors_ref = oracle.greedy_color_stride(c, stride)
+            assert k == k_ref
+            np.testing.assert_array_equal(colors, colors_ref)
+            assert oracle.check_coloring(c, colors, k) == 0
+            if stride > 0:
+                assert oracle.max_class_gap(colors, k) <= stride
+            h.ncolors = k
+            x = fe.source_vector(m.n, 7)
+            for tr in (False, True):
+                _check(m, x, h.run(x, "color", tr), tr, TOL["f64"])
+        finally:
+            h.close()
+
+
+def test_colour_product_many_classes(cs):
+    # stride 1 on a P1 grid gives hundreds of classes: hundreds of grid barriers in one launch;
+    # integer values make the result exact
+    m = fe.p1_grid(30, 30, 11)
+    mi = fe.FEMatrix(m.n, m.row_ptr, m.col, fe.integer_values(m.row_ptr, m.col, 12))
+    xi = fe.integer_vector(m.n, 13)
+    for storage in ("f64", "f32", "bf16"):
+        h = Handle(cs, mi, storage)
+        try:
+            h.ncolors = cs.csrc_color_stride(h.h, 1)
+            assert h.ncolors > 100
+            for tr in (False, True):
+                np.testing.assert_array_equal(h.run(xi, "color", tr), _ref(mi, xi, tr))
+        finally:
+            h.close()
