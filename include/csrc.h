@@ -429,7 +429,9 @@ csrc_status csrc_get_kernel_times(csrc_handle h, csrc_kernel_times* out);
  * Square handles only. Synchronises the stream every iteration (the scalars go to the
  * host). The handle keeps six scratch vectors for later calls.
  * Errors: INVALID_ARG, ALIAS, NOT_PARTITIONED, NOT_COLORED, OUT_OF_MEMORY, CUDA, and
- * NOT_CONVERGED / BREAKDOWN (outputs and x still set).
+ * NOT_CONVERGED / BREAKDOWN (outputs and x still set); a device error raised by the products
+ * during the solve (DEVICE_TIMEOUT, DEVICE_BOUNDS, RANGE) is returned and cleared from the
+ * handle's status word.
  */
 csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_t maxit, csrc_strategy strategy,
                       int32_t* iters_out, double* relres_out, cudaStream_t stream);

@@ -2162,6 +2162,15 @@ csrc_status csrc_bicg(csrc_handle h, const void* b, void* x, double rtol, int32_
   auto finish = [&](int32_t it, csrc_status st) {
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = bb > 0.0 ? std::sqrt(nrm2 / bb) : 0.0;
+    // the products' device status word: an error raised during the solve is returned here
+    // (and cleared) rather than left for a later call to find
+    int32_t w = 0;
+    if (cudaMemcpy(&w, h->d_status, 4, cudaMemcpyDeviceToHost) == cudaSuccess && w != 0) {
+      cudaMemset(h->d_status, 0, 4);
+      if (w & DEV_TIMEOUT) return CSRC_ERR_DEVICE_TIMEOUT;
+      if (w & DEV_BOUNDS) return CSRC_ERR_DEVICE_BOUNDS;
+      if (w & DEV_RANGE) return CSRC_ERR_RANGE;
+    }
     return st;
   };
   if (nrm2 <= tol2) return finish(0, CSRC_OK);

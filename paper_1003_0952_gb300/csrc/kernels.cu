@@ -58,7 +58,10 @@ __global__ void split_df_kernel(const double* __restrict__ v, df32* __restrict__
 
 cudaError_t launch_split_df(const double* v, void* out, int64_t count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 32);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)std::max(sms, 1) * 32);
   split_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, static_cast<df32*>(out), count);
   return cudaGetLastError();
 }

@@ -136,3 +136,58 @@ def test_batch_256_graph(cs):
     finally:
         for h in hs:
             cs.csrc_destroy(h)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_q1v_reduced_storage(cs, storage):
+    # q1v_96 with FP32 / BF16 storage (float vectors), A x and A^T x, window strategy
+    builder, xseed = fe.CONFIGS["q1v_96"]
+    m = builder()
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, xseed).astype(np.float32).astype(np.float64)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+    try:
+        for tr in (False, True):
+            ref = (oracle.csrc_spmv_t if tr else oracle.csrc_spmv)(c, x)
+            err = oracle.max_rel_err(m, x, _product(cs, h, x, storage, "window", tr), ref, transpose=tr)
+            print(f"q1v_96 {storage} transpose={tr}: max rel err {err:.3e}")
+            assert err <= TOL[storage], (tr, err)
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_q1v_reduced_precision_on_double_vectors(cs):
+    # q1v_96 FP64 handle run at FP32 and BF16 precision (csrc_set_precision): double vectors
+    builder, xseed = fe.CONFIGS["q1v_96"]
+    m = builder()
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, xseed)
+    ref = oracle.csrc_spmv(c, x)
+    h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64)
+    try:
+        for prec in ("f32", "bf16"):
+            cs.csrc_set_precision(h, cs.STORAGE[prec])
+            err = oracle.max_rel_err(m, x, _product(cs, h, x, "f64", "window", False), ref)
+            bound = cs.csrc_get_info(h)["error_bound"]
+            print(f"q1v_96 f64 handle at {prec}: max rel err {err:.3e} (bound {bound:.3e})")
+            assert err <= min(TOL[prec], bound), (prec, err, bound)
+    finally:
+        cs.csrc_destroy(h)
+
+
+def test_delaunay_2m(cs):
+    # C3 as stated: Delaunay of 2M uniform points in the unit cube, RCM order; FP64, FP32 and
+    # BF16 storage, A x and A^T x (the host generation takes a few minutes)
+    m = fe.tet_mesh(2_000_000, 1003, method="delaunay")
+    c = oracle.from_matrix(m)
+    x = fe.source_vector(m.n, 2003).astype(np.float32).astype(np.float64)
+    refs = {False: oracle.csrc_spmv(c, x), True: oracle.csrc_spmv_t(c, x)}
+    for storage in ("f64", "f32", "bf16"):
+        h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+        try:
+            for tr in (False, True):
+                err = oracle.max_rel_err(m, x, _product(cs, h, x, storage, "window", tr), refs[tr], transpose=tr)
+                print(f"tet_delaunay_2m {storage} transpose={tr}: max rel err {err:.3e}")
+                assert err <= TOL[storage], (storage, tr, err)
+        finally:
+            cs.csrc_destroy(h)
