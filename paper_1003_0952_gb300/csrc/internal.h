@@ -169,6 +169,12 @@ struct DevPlan {
 // of every lane whose list is longer than m, contiguously, so that a warp's loads of one
 // step are coalesced.
 constexpr int kOwnerLanes = 32;
+// The regular part of a slice (the steps below its shortest list, where all 32 lanes are
+// active) is stored in blocks of kOwnerBlock steps with each lane's steps side by side: entry
+// (m, lane) at slice start + 32 * kOwnerBlock * (m / kOwnerBlock) + kOwnerBlock * lane + m % kOwnerBlock,
+// so that a lane reads a block with vector loads; slices start on a block boundary, and the
+// ragged tail (jagged-diagonal order) follows the regular part.
+constexpr int kOwnerBlock = 4;
 constexpr uint32_t kOwnerPadSlot = 0xffffu;  // lane word slot of an unused lane (length 0)
 constexpr int kOwnerMaxSlots = 65535;         // slots are 16-bit; 0xffff marks unused lanes
 constexpr int kOwnerMaxLength = 65535;        // list lengths are 16-bit
@@ -198,6 +204,7 @@ struct OwnerPlan {
   int32_t max_len = 0;       // longest entry list
   int32_t max_parts = 1;     // most partial sums of one row (its own band's and the spilled ones)
   int64_t entries = 0;       // list entries of all bands (n + 2h)
+  int64_t capacity = 0;      // length of the entry arrays (entries plus block-alignment gaps)
   int64_t lane_steps = 0;    // sum over slices of 32 * longest list (FMA lanes issued)
   int64_t nslices = 0;
   int64_t spill = 0;         // spill slots of all bands

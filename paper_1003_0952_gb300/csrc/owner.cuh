@@ -131,17 +131,48 @@ __device__ __forceinline__ void owner_fma_batch(const A* xs, int m0, int len, co
   }
 }
 
-// Loads of the U steps of batch bi of a slice's regular part (every lane active): entry
-// (m, lane) is at pS[32 m] / pV[32 m], pS and pV pointing at the lane's entry of step 0.
+// Block loads: the kOwnerBlock (= 4) consecutive slots / values of one lane's block, with
+// vector loads (the block starts on a multiple of 4 entries).
+__device__ __forceinline__ void owner_ld_block(const uint16_t* p, uint32_t (&s)[4]) {
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+  s[0] = w.x & 0xffffu;
+  s[1] = w.x >> 16;
+  s[2] = w.y & 0xffffu;
+  s[3] = w.y >> 16;
+}
+__device__ __forceinline__ void owner_ldv_block(const double* p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void owner_ldv_block(const float* p, float (&v)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void owner_ldv_block(const uint16_t* p, uint16_t (&v)[4]) {
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+  v[0] = (uint16_t)(w.x & 0xffffu);
+  v[1] = (uint16_t)(w.x >> 16);
+  v[2] = (uint16_t)(w.y & 0xffffu);
+  v[3] = (uint16_t)(w.y >> 16);
+}
+
+// Loads of block bi of a slice's regular part (every lane active): the lane's kOwnerBlock
+// steps lie side by side at pS / pV + 32 * kOwnerBlock * bi, pS and pV pointing at the lane's
+// first block.
 template <typename V, int U>
 __device__ __forceinline__ void owner_load_full(const uint16_t* __restrict__ pS, const V* __restrict__ pV, int bi,
                                                 uint32_t (&sv)[U], V (&vv)[U]) {
-  const int m0 = bi * U;
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    sv[u] = owner_ld(pS + (size_t)kOwnerLanes * (m0 + u));
-    vv[u] = owner_ldv(pV + (size_t)kOwnerLanes * (m0 + u));
-  }
+  static_assert(U == kOwnerBlock, "a batch is one block");
+  const size_t o = (size_t)kOwnerLanes * kOwnerBlock * bi;
+  owner_ld_block(pS + o, sv);
+  owner_ldv_block(pV + o, vv);
 }
 
 // The multiply-adds of a full batch (every step active for this lane).
@@ -167,11 +198,10 @@ __device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)
   }
 }
 
-// Steps per batch of loads (two batches are in flight per warp): deeper for 4- and 2-byte
-// values, whose multiply-adds are too quick to hide a batch's latency on their own.
+// Steps per batch of loads: one block (two batches are in flight per warp).
 template <int ST>
 constexpr int owner_unroll(int rk) {
-  return rk == 1 ? 4 : (ST == OM_F64 ? 4 : 6);
+  return rk > 0 ? kOwnerBlock : kOwnerBlock;
 }
 
 // Band b of the product described by a, run by the whole CTA.
@@ -234,12 +264,13 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
     A acc[RK];
 #pragma unroll
     for (int c = 0; c < RK; ++c) acc[c] = A(0);
-    // Regular part: steps m < minlen hold all 32 lanes, entry (m, lane) at base + 32 m + lane,
-    // so each lane walks one pointer with fixed offsets. Two batches of U steps are in flight
+    // Regular part: the steps of whole blocks below minlen hold all 32 lanes, each lane's steps
+    // of a block side by side (internal.h), so each lane reads a block with vector loads. Two
+    // batches (blocks) of U steps are in flight
     // in a ring of registers: a batch's loads are issued two compute phases before its
     // multiply-adds, so that memory latency overlaps this and other warps' arithmetic.
-    const uint16_t* __restrict__ pS = S + base + lane;
-    const V* __restrict__ pV = Vv + base + lane;
+    const uint16_t* __restrict__ pS = S + base + kOwnerBlock * lane;
+    const V* __restrict__ pV = Vv + base + kOwnerBlock * lane;
     const int nfull = minlen / U;  // batches of U steps with every lane active
     {
       uint32_t s0[U], s1[U];

@@ -88,11 +88,11 @@ struct Layout {
   std::vector<int64_t> band_entry;  // first entry of each band (nb + 1)
 };
 
-// Second pass: the lists of band b, written at its offsets. Returns false when a list
-// is longer than kOwnerMaxLength.
+// Second pass: the lists of band b, written in its region [e0, e_end) of the entry arrays.
+// Returns false when a list is longer than kOwnerMaxLength.
 bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, const PlanBand& pb, const int4& bd,
-               int32_t q0, int64_t e0, Scratch& sc, int64_t* slice_off, uint32_t* lane, uint16_t* S, int64_t* code,
-               int32_t* spill_row, int64_t* lane_steps) {
+               int32_t q0, int64_t e0, int64_t e_end, Scratch& sc, int64_t* slice_off, uint32_t* lane, uint16_t* S,
+               int64_t* code, int32_t* spill_row, int64_t* lane_steps) {
   const int32_t r0 = pb.r0, r1 = pb.r1;
   collect_spill_rows(ia, ja, r0, r1, sc);
   const int32_t nsp = (int32_t)sc.sp.size();
@@ -143,11 +143,18 @@ bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, c
         lw[l] = kOwnerPadSlot;  // length 0
       }
     }
+    E = (E + kOwnerBlock - 1) / kOwnerBlock * kOwnerBlock;  // slices start on a block boundary
     slice_off[(size_t)q0 + q] = E;
+    const int64_t base = E;
     const int32_t maxlen = sc.len[(size_t)sc.order[(size_t)a]];
+    // regular part: the steps below the shortest list (lane 31's; 0 when lanes are unused), in
+    // whole blocks of kOwnerBlock steps, each lane's steps of a block side by side
+    const int32_t minlen = cnt == kOwnerLanes ? sc.len[(size_t)sc.order[(size_t)a + cnt - 1]] : 0;
+    const int32_t regular = minlen / kOwnerBlock * kOwnerBlock;
     *lane_steps += (int64_t)kOwnerLanes * maxlen;
     int32_t active = cnt;  // lanes whose list is longer than m (a prefix: lengths descend)
     for (int32_t m = 0; m < maxlen; ++m) {
+      if (m == regular) E = base + (int64_t)kOwnerLanes * regular;  // the ragged tail follows
       while (active > 0 && sc.len[(size_t)sc.order[(size_t)a + active - 1]] <= m) --active;
       for (int32_t l = 0; l < active; ++l) {
         const int32_t t = sc.order[(size_t)a + l];
@@ -175,13 +182,17 @@ bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, c
           c = ((int64_t)(k0 + sc.upk[(size_t)qq]) << 2) | 2;  // scattered pair: au[k] with x of its row
           s = nsp + (sc.upr[(size_t)qq] - r0);
         }
-        S[(size_t)E + l] = (uint16_t)s;
-        code[(size_t)E + l] = c;
+        const int64_t pos = m < regular ? base + (int64_t)kOwnerLanes * kOwnerBlock * (m / kOwnerBlock) +
+                                              (int64_t)kOwnerBlock * l + m % kOwnerBlock
+                                        : E + l;
+        S[(size_t)pos] = (uint16_t)s;
+        code[(size_t)pos] = c;
       }
-      E += active;
+      if (m >= regular) E += active;
     }
+    if (regular == maxlen) E = base + (int64_t)kOwnerLanes * regular;
   }
-  return true;
+  return E <= e_end;
 }
 
 template <typename T>
@@ -246,7 +257,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   L.band.resize((size_t)nb);
   L.band_slice.assign((size_t)nb + 1, 0);
   L.band_entry.assign((size_t)nb + 1, 0);
-  int64_t spill = 0;
+  int64_t spill = 0, entries_used = 0;
   int32_t max_slots = 0;
   for (int32_t b = 0; b < nb; ++b) {
     const PlanBand& pb = bands[(size_t)b];
@@ -260,8 +271,11 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
     if (spill > (int64_t)INT32_MAX - 1) return CSRC_ERR_NOT_PARTITIONED;
     max_slots = std::max(max_slots, nslots);
     L.band_slice[(size_t)b + 1] = L.band_slice[(size_t)b] + (nslots + kOwnerLanes - 1) / kOwnerLanes;
-    L.band_entry[(size_t)b + 1] =
-        L.band_entry[(size_t)b] + nown + 2 * ((int64_t)ia[(size_t)pb.r1] - ia[(size_t)pb.r0]);
+    // the band's region: its entries plus room to start every slice on a block boundary
+    const int64_t need = nown + 2 * ((int64_t)ia[(size_t)pb.r1] - ia[(size_t)pb.r0]) +
+                         (int64_t)(kOwnerBlock - 1) * ((nslots + kOwnerLanes - 1) / kOwnerLanes);
+    L.band_entry[(size_t)b + 1] = L.band_entry[(size_t)b] + (need + kOwnerBlock - 1) / kOwnerBlock * kOwnerBlock;
+    entries_used += nown + 2 * ((int64_t)ia[(size_t)pb.r1] - ia[(size_t)pb.r0]);
   }
   const int64_t nslices = L.band_slice[(size_t)nb];
   const int64_t entries = L.band_entry[(size_t)nb];
@@ -280,8 +294,8 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
       const int32_t b = next.fetch_add(1);
       if (b >= nb) break;
       if (!fill_band(ia, ja, bands[(size_t)b], L.band[(size_t)b], L.band_slice[(size_t)b],
-                     L.band_entry[(size_t)b], sc, slice_off.data(), lane.data(), S.data(), code.data(),
-                     spill_row.data(), &steps[(size_t)w]))
+                     L.band_entry[(size_t)b], L.band_entry[(size_t)b + 1], sc, slice_off.data(), lane.data(),
+                     S.data(), code.data(), spill_row.data(), &steps[(size_t)w]))
         fits = false;
     }
   });
@@ -305,7 +319,8 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
   p.rk = rk;
   p.mode = mode;
   for (int64_t q = 0; q < nslices; ++q) p.max_len = std::max<int32_t>(p.max_len, (int32_t)(lane[(size_t)q * kOwnerLanes] >> 16));
-  p.entries = entries;
+  p.entries = entries_used;
+  p.capacity = entries;
   p.nslices = nslices;
   p.spill = spill;
   p.max_slots = max_slots;
