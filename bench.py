@@ -349,7 +349,7 @@ def run_ours(args):
     peak, peak_src = measured_hbm()
     nprod, ms_prod = ktimes["product"]
     # algorithmic bytes of one product-kernel launch: the CSRC working set (Table 1's ws) plus
-    # the spill writes of the bands (SURVEY.md's accumulation traffic counted explicitly)
+    # the spill writes of the bands (the accumulation's traffic, counted explicitly)
     vec_bytes = 8 if args.storage == "f64" else 4
     kbytes = int(info["model_bytes"]) + vec_bytes * int(info["spill_entries"])
     launch_ms = ms_prod / max(nprod, 1)
@@ -465,7 +465,7 @@ def run_suite(args):
     def gpu(t):
         return t.double().cpu().numpy()
 
-    def spmv_rows(name, m, storages, strategies, colour=False):
+    def spmv_rows(name, m, storages, strategies, colour=False, flags=0):
         xs = fe.source_vector(m.n, 7)
         c = oracle.from_matrix(m)
         for storage in storages:
@@ -475,7 +475,7 @@ def run_suite(args):
             mb = model_bytes(m.n, m.pairs, vb, xb)
             (yref, ytref), cpu = _oracle_leg(lambda: (oracle.csrc_spmv(c, x64), oracle.csrc_spmv_t(c, x64)),
                                              2 * model_bytes(m.n, m.pairs))
-            h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage])
+            h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage], flags)
             try:
                 cs.csrc_partition(h, 0)
                 if colour:
@@ -547,6 +547,11 @@ def run_suite(args):
             m, _ = build_workload(wl)
             spmv_rows(f"C2 {wl}", m, ["f64", "f32", "bf16"] if wl == "q1v_96" else ["f64"], strategies,
                       colour=True)
+            if wl == "q1v_96":
+                # the stream-order kernel with double-float arithmetic (narrower than FP64:
+                # about 2^-46 per operation), labelled as such
+                spmv_rows("C2 q1v_96 double-float arithmetic (CSRC_FLAG_DF32_ARITH)", m, ["f64"],
+                          ["window_atomic"], flags=cs.CSRC_FLAG_DF32_ARITH)
             del m
     if "c3" in sel:
         m = fe.tet_mesh(2_000_000, 1003, method=args.tet_method)
@@ -722,17 +727,23 @@ def run_suite(args):
         refs, cpu = _oracle_leg(lambda: [oracle.csrc_spmv(c, x) for c, x in zip(cs_list, xs)],
                                 sum(model_bytes(m.n, m.pairs) for m in ms_list))
         res = {}
-        for storage in ("f32", "f64"):
+        for storage, tuned in (("f32", False), ("f32", True), ("f64", False)):
             hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[storage]) for m in ms_list]
             try:
                 dt = torch.float64 if storage == "f64" else torch.float32
                 X = [torch.from_numpy(x).to(dt).cuda() for x in xs]
                 Y = [torch.empty_like(x) for x in X]
                 if storage == "f32":
-                    for h, x, y in zip(hs, X, Y):
-                        cs.csrc_autotune(h, x, y, sptr)
+                    how = "one CUDA-graph replay over all 256 members"
+                    if tuned:
+                        # members keep the strategy csrc_autotune picked for their single products
+                        for h, x, y in zip(hs, X, Y):
+                            cs.csrc_autotune(h, x, y, sptr)
+                        how += ", each member at the strategy csrc_autotune picked for its single products"
+                    else:
+                        how += ", window strategy for every member (the default)"
                     ms = _events_ms(lambda: cs.csrc_spmm_batched(hs, X, Y, 1, False, sptr), args.suite_iters)
-                    vb, xb, how = 4, 4, "one CUDA-graph replay over all 256 members"
+                    vb, xb = 4, 4
                 else:
                     for h in hs:
                         cs.csrc_partition(h, 0)
@@ -748,7 +759,7 @@ def run_suite(args):
                                              gpu(y), ref)
                           for m, x, y, ref in zip(ms_list, xs, Y, refs))
                 mb = sum(model_bytes(m.n, m.pairs, vb, xb) for m in ms_list)
-                res[storage] = ms
+                res[storage + ("_tuned" if tuned else "")] = ms
                 emit({"suite": "C5 batch_256", "storage": storage, "how": how, "members": len(ms_list),
                       "sum_n": tot_n, "sum_pairs": tot_pairs, "ms_per_batch": ms, "GB/s": mb / ms / 1e6,
                       "GFLOP/s": flops(tot_n, tot_pairs) / ms / 1e6, "max_rel_err": err,
@@ -756,7 +767,33 @@ def run_suite(args):
             finally:
                 for h in hs:
                     cs.csrc_destroy(h)
-        emit({"suite": "C5 batch_256 speedup", "f32_graph_vs_f64_separate": res["f64"] / res["f32"]})
+        # the mixed-precision batched form on double vectors: FP64 handles, each at the precision
+        # csrc_autotune_precision picks under a componentwise budget of 1e-5, all in one graph
+        hs = [cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.CSRC_F64) for m in ms_list]
+        try:
+            X = [torch.from_numpy(x).cuda() for x in xs]
+            Y = [torch.empty_like(x) for x in X]
+            picks = {}
+            for h, x, y in zip(hs, X, Y):
+                p_, _ = cs.csrc_autotune_precision(h, x, y, 1e-5, sptr)
+                picks[p_] = picks.get(p_, 0) + 1
+            ms = _events_ms(lambda: cs.csrc_spmm_batched(hs, X, Y, 1, False, sptr), args.suite_iters)
+            torch.cuda.synchronize()
+            err = max(oracle.max_rel_err(m, x, gpu(y), ref) for m, x, y, ref in zip(ms_list, xs, Y, refs))
+            mb = sum(model_bytes(m.n, m.pairs) for m in ms_list)  # the FP64 model: what the FP64 path moves
+            res["mixed"] = ms
+            emit({"suite": "C5 batch_256", "storage": "f64 handles, per-matrix precision (budget 1e-5)",
+                  "how": "one CUDA-graph replay over all 256 members, each at its tuned precision",
+                  "precisions": {{0: "f64", 1: "f32", 2: "bf16"}[k]: v for k, v in picks.items()},
+                  "members": len(ms_list), "ms_per_batch": ms, "GB/s (FP64 model)": mb / ms / 1e6,
+                  "GFLOP/s": flops(tot_n, tot_pairs) / ms / 1e6, "max_rel_err": err, "tolerance": 1e-5,
+                  "cpu_baseline": cpu})
+        finally:
+            for h in hs:
+                cs.csrc_destroy(h)
+        emit({"suite": "C5 batch_256 speedup", "f32_graph_vs_f64_separate": res["f64"] / res["f32"],
+              "f32_graph_autotuned_members_vs_f64_separate": res["f64"] / res["f32_tuned"],
+              "mixed_precision_graph_vs_f64_separate": res["f64"] / res["mixed"]})
     return 0
 
 
