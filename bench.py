@@ -276,6 +276,8 @@ def run_ours(args):
     h = cs.csrc_create_from_csr(m.n, m.row_ptr, m.col, m.val, cs.STORAGE[args.storage])
     try:
         cs.csrc_partition(h, 0)
+        if args.strategy == "color":
+            cs.csrc_color(h, 12345)
         info = cs.csrc_get_info(h)
         stream = torch.cuda.current_stream()
         sptr = stream.cuda_stream
@@ -349,9 +351,11 @@ def run_ours(args):
     peak, peak_src = measured_hbm()
     nprod, ms_prod = ktimes["product"]
     # algorithmic bytes of one product-kernel launch: the CSRC working set (Table 1's ws) plus
-    # the spill writes of the bands (the accumulation's traffic, counted explicitly)
+    # the spill writes of the bands (the accumulation's traffic, counted explicitly); the colour
+    # product writes y in place and spills nothing
     vec_bytes = 8 if args.storage == "f64" else 4
-    kbytes = int(info["model_bytes"]) + vec_bytes * int(info["spill_entries"])
+    colour = args.strategy == "color"
+    kbytes = int(info["model_bytes"]) + (0 if colour else vec_bytes * int(info["spill_entries"]))
     launch_ms = ms_prod / max(nprod, 1)
     achieved = kbytes / (launch_ms * 1e-3) / 1e9 if nprod else None
     launches = sum(v[0] for v in ktimes.values())
@@ -361,9 +365,16 @@ def run_ours(args):
     window = args.strategy in ("window", "auto") and info["tuned_strategy"] in (0, 1)
     arith = ("FP64 pipe: one FP64 multiply-add per stored value" if args.storage == "f64" and
              (window or info["arith"] == 1) else {0: "double-float (FP32 pairs)", 1: "FP64 pipe", 2: "FP32"}[info["arith"]])
+    if colour and args.storage == "f64":
+        arith = "FP64 pipe"
     cfg.update({"nbands": info["nbands"], "spill_entries": info["spill_entries"], "arith": arith,
                 "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"})
+    if args.strategy != "window":
+        cfg["strategy"] = {"auto": "auto (the handle's tuned strategy)", "window_atomic": "window-atomic (stream order)",
+                           "atomic": "atomic (stream order)",
+                           "color": f"colour ({info['ncolors']} classes, one cooperative launch)"}[args.strategy]
     kname = ("owner_kernel (window strategy: target-sorted entry lists, one lane per window row)" if window
+             else "color_persistent_kernel (colour strategy: all classes in one cooperative launch)" if colour
              else "band_kernel (stream-order strategy)")
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -804,7 +815,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="q1v_96")
-    ap.add_argument("--strategy", default="window", choices=["auto", "window", "window_atomic", "atomic"])
+    ap.add_argument("--strategy", default="window", choices=["auto", "window", "window_atomic", "atomic", "color"])
     ap.add_argument("--storage", default="f64", choices=["f64", "f32", "bf16"],
                     help="value storage: f64 (the default workload), or f32 / bf16 with float vectors")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -340,7 +340,9 @@ csrc_status csrc_set_precision(csrc_handle h, csrc_dtype precision);
  * multiply-adds (2^-53 for FP64; 2^-24 for FP32; 2^-8 for BF16 values), L the longest row of A
  * and P the most partial sums any row is split into across bands. Every precision within the
  * budget is timed on the caller's device vectors x, y (y is overwritten), and the fastest is
- * kept (csrc_set_precision). The decision is kept in the tuning cache (csrc_autotune).
+ * kept (csrc_set_precision); a wider precision must be more than 3 % faster than a narrower
+ * one to be preferred, so near-ties keep the fewer bytes. The decision is kept in the tuning
+ * cache (csrc_autotune).
  *   chosen_out  host (nullable): the csrc_dtype picked
  *   bound_out   host (nullable): its error bound
  * Synchronous on stream. Errors: INVALID_ARG (null or host pointers, max_rel_err <= 0, or no

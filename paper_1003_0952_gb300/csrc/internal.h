@@ -385,8 +385,15 @@ cudaError_t launch_jp_round(int32_t n, const int32_t* ia, const int32_t* ja, con
 // (barrier: a zeroed counter), `group` lanes per row. A barrier wait that runs out sets
 // DEV_TIMEOUT in *status.
 int color_group(double mean_pairs);
-cudaError_t launch_color_spmv(int storage, int group, int32_t ncolors, const int32_t* color_ptr, const int32_t* rows,
-                              const int32_t* ia, const int32_t* ja, const void* al, const void* au, const void* ad,
-                              const void* x, void* y, unsigned* barrier, int32_t* status, cudaStream_t s);
+// The class-ordered copy of the lists: for the n rows of the class order, desc[t] = {i, k0, k1,
+// ia[i]}; pairs ia[i] .. ia[i+1] - 1 of ja, al and au (au may be null) go to k0 .. k1 - 1 of
+// cja, cal and cau. vbytes: 8, 4 or 2.
+cudaError_t launch_color_copy(int vbytes, const int4* desc, int32_t n, const int32_t* ja, const void* al,
+                              const void* au, int32_t* cja, void* cal, void* cau, cudaStream_t s);
+// The colour-ordered product over the class-ordered copy (desc, ja, al = gathered values, au =
+// scattered values).
+cudaError_t launch_color_spmv(int storage, int group, int32_t ncolors, const int32_t* color_ptr, const int4* desc,
+                              const int32_t* ja, const void* al, const void* au, const void* ad, const void* x,
+                              void* y, unsigned* barrier, int32_t* status, cudaStream_t s);
 
 }  // namespace csrc

@@ -200,8 +200,8 @@ __device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)
 
 // Steps per batch of loads: one block (two batches are in flight per warp).
 template <int ST>
-constexpr int owner_unroll(int rk) {
-  return rk > 0 ? kOwnerBlock : kOwnerBlock;
+constexpr int owner_unroll(int) {
+  return kOwnerBlock;
 }
 
 // Band b of the product described by a, run by the whole CTA.
@@ -253,14 +253,30 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
   const uint16_t* __restrict__ S = a.S;
   const V* __restrict__ Vv = static_cast<const V*>(a.V);
   const int q1 = __ldg(a.band_slice + b + 1);
-  for (int q = __ldg(a.band_slice + b) + warp; q < q1; q += W) {
-    const uint32_t w = __ldg(a.lane + (size_t)q * kOwnerLanes + lane);
+  // a slice's lane word and list offset are loaded one slice ahead, so that a warp's next
+  // slice starts with its list loads (short lists, as in wide-bandwidth orderings, make
+  // many slices of a few steps each)
+  int q = __ldg(a.band_slice + b) + warp;
+  uint32_t wn = 0;
+  int64_t basen = 0;
+  if (q < q1) {
+    wn = __ldg(a.lane + (size_t)q * kOwnerLanes + lane);
+    basen = __ldg(a.slice_off + q);
+  }
+  for (; q < q1; q += W) {
+    const uint32_t w = wn;
+    const int64_t base = basen;
+    if (q + W < q1) {
+      wn = __ldg(a.lane + (size_t)(q + W) * kOwnerLanes + lane);
+      basen = __ldg(a.slice_off + q + W);
+    }
     const int len = (int)(w >> 16);
     const int slot = (int)(w & 0xffffu);
+    // a spill row's position in the spill buffer, read now and used after the list
+    const int spos = slot < nsp ? __ldg(a.spill_pos + sbase + slot) : 0;
     // lengths descend across the slice: lane 0 has the longest list, lane 31 the shortest
     const int maxlen = __shfl_sync(0xffffffffu, len, 0);
     const int minlen = __shfl_sync(0xffffffffu, len, 31);
-    const int64_t base = __ldg(a.slice_off + q);
     A acc[RK];
 #pragma unroll
     for (int c = 0; c < RK; ++c) acc[c] = A(0);
@@ -296,7 +312,7 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
       owner_fma_batch<A, V, U, RK>(xs, m0, len, sv, vv, acc);
     }
     if (slot < nsp) {
-      A* sp = static_cast<A*>(a.spill) + (size_t)__ldg(a.spill_pos + sbase + slot) * a.lds;
+      A* sp = static_cast<A*>(a.spill) + (size_t)spos * a.lds;
 #pragma unroll
       for (int c = 0; c < RK; ++c) sp[c] = acc[c];
     } else if (slot != (int)kOwnerPadSlot) {

@@ -463,6 +463,8 @@ def test_double_float_range_is_reported(cs):
         for s in ("window", "window_atomic", "atomic"):
             for xx in (x, x2):
                 _check(m, xx, h.run(xx, s), False, TOL["f64"])
+        torch.cuda.synchronize()
+        assert cs.csrc_get_last_device_error(h.h) == cs.CSRC_OK  # no false range error
     finally:
         h.close()
     # matrix values outside the double-float range switch a double-float handle to FP64 arithmetic
