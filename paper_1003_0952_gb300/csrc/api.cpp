@@ -543,8 +543,11 @@ int32_t owner_auto_bands(const csrc_matrix_s* h, int rk) {
     return (int32_t)std::min<int64_t>(std::max<int64_t>(1, (nnz + kOwnerBandNnz - 1) / kOwnerBandNnz),
                                       std::max<int32_t>(1, h->n));
   }
+  // FP32 / BF16 values leave room for larger bands (fewer spills; measured on q1v_96: 1,216
+  // bands against 2,432 for FP64, whose product the FP64 pipe bounds)
+  const int64_t target = h->owner_mode() == OM_F64 ? kOwnerBandNnz : kOwnerBandNnz * 9 / 5;
   const int64_t slots = (int64_t)h->sms * owner_ctas_per_sm(rk);
-  int64_t waves = (nnz + slots * kOwnerBandNnz - 1) / (slots * kOwnerBandNnz);
+  int64_t waves = (nnz + slots * target - 1) / (slots * target);
   if (waves < 1) waves = 1;
   return (int32_t)std::min<int64_t>(slots * waves, std::max<int32_t>(1, h->n));
 }
@@ -552,11 +555,29 @@ int32_t owner_auto_bands(const csrc_matrix_s* h, int rk) {
 // Owner lists for rk columns per pass from the Section 3.1 partition into nbands bands
 // (0 = automatic); bands whose windows exceed shared memory are split further.
 csrc_status build_owner(csrc_matrix_s* h, int rk, int32_t nbands, OwnerPlan& p, std::vector<int32_t>* part_out) {
-  const int32_t nb = nbands > 0 ? std::min<int32_t>(nbands, std::max<int32_t>(1, h->n)) : owner_auto_bands(h, rk);
+  int32_t nb = nbands > 0 ? std::min<int32_t>(nbands, std::max<int32_t>(1, h->n)) : owner_auto_bands(h, rk);
   std::vector<int32_t> part;
   nnz_partition(h->ia, 0, h->n, nb, part);
   CSRC_TRY_S(build_owner_plan(h->n, h->h, h->ia, h->ja, part, rk, h->owner_mode(), owner_smem_budget(rk),
                               (int)h->vbytes(), h->d_al, h->au_ptr(), h->d_ad, h->sym, p));
+  // An automatic single-column count whose windows did not fit was split band by band, which
+  // leaves halves beside whole bands (uneven work in the last wave). Partition again into the
+  // next whole number of waves at or above the split count, so that every band is about equal
+  // (Delaunay 2M in FP64: 608 bands split into 1,202, then 1,216 equal bands: 0.143 -> 0.110 ms).
+  const int64_t slots = (int64_t)h->sms * owner_ctas_per_sm(rk);
+  for (int it = 0; nbands <= 0 && rk == 1 && it < 3 && p.nb > nb; ++it) {
+    const int32_t nb2 = (int32_t)std::min<int64_t>((p.nb + slots - 1) / slots * slots, std::max<int32_t>(1, h->n));
+    if (nb2 <= nb) break;
+    OwnerPlan q;
+    std::vector<int32_t> part2;
+    nnz_partition(h->ia, 0, h->n, nb2, part2);
+    CSRC_TRY_S(build_owner_plan(h->n, h->h, h->ia, h->ja, part2, rk, h->owner_mode(), owner_smem_budget(rk),
+                                (int)h->vbytes(), h->d_al, h->au_ptr(), h->d_ad, h->sym, q));
+    free_owner_plan(p);
+    p = std::move(q);
+    part.swap(part2);
+    nb = nb2;
+  }
   if (part_out) part_out->swap(part);
   return CSRC_OK;
 }
@@ -1912,15 +1933,18 @@ csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t st
       CSRC_TRY(cudaEventElapsedTime(ms, e0, e1));
       return CSRC_OK;
     };
-    // the window strategy with the automatic band count, half and twice as many bands;
-    // then the stream-order strategies, and the colour strategy when the rows are coloured
+    // the window strategy with the automatic band count (0; or the partition's count), one
+    // wave of bands fewer and one more; then the stream-order strategies, and the colour
+    // strategy when the rows are coloured
     float best = 1e30f;
     int32_t best_nb = 0, best_st = CSRC_STRAT_WINDOW;
     csrc_status st = CSRC_OK;
     const int32_t nb0 = h->part_nbands > 0 ? h->part_nbands : owner_auto_bands(h, 1);
-    const int32_t counts[3] = {nb0, std::max(1, nb0 / 2), nb0 * 2};
+    const int32_t wave = std::max<int32_t>(1, h->sms * owner_ctas_per_sm(1));
+    const int32_t counts[3] = {h->part_nbands > 0 ? nb0 : 0, nb0 > wave ? nb0 - wave : std::max(1, nb0 / 2),
+                               nb0 + wave};
     for (int32_t nb : counts) {
-      if (nb > h->n && nb != nb0) continue;
+      if (nb > h->n) continue;
       h->owner_nbands = nb;
       drop_owner_plans(h);
       OwnerPlan* op = nullptr;
