@@ -170,10 +170,12 @@ struct DevPlan {
 // step are coalesced.
 constexpr int kOwnerLanes = 32;
 // The regular part of a slice (the steps below its shortest list, where all 32 lanes are
-// active) is stored in blocks of kOwnerBlock steps with each lane's steps side by side: entry
-// (m, lane) at slice start + 32 * kOwnerBlock * (m / kOwnerBlock) + kOwnerBlock * lane + m % kOwnerBlock,
-// so that a lane reads a block with vector loads; slices start on a block boundary, and the
-// ragged tail (jagged-diagonal order) follows the regular part.
+// active) is stored in blocks of B steps with each lane's steps side by side: entry (m, lane)
+// at slice start + 32 * B * (m / B) + B * lane + m % B, so that a lane reads a block with
+// vector loads; slices start on a block boundary, and the ragged tail (jagged-diagonal order)
+// follows the regular part. B = owner_block(mode, rk): 8 steps for 2-byte values in single-
+// column passes (one 16-byte load of slots and one of values; measured 9 % faster on q1v_96 in
+// BF16, 3-4 % slower for rk > 1 and for the short lists of a Delaunay mesh), 4 otherwise.
 constexpr int kOwnerBlock = 4;
 constexpr uint32_t kOwnerPadSlot = 0xffffu;  // lane word slot of an unused lane (length 0)
 constexpr int kOwnerMaxSlots = 65535;         // slots are 16-bit; 0xffff marks unused lanes
@@ -189,6 +191,10 @@ constexpr int kOwnerModes = 5;
 inline int owner_value_bytes(int mode) { return mode == OM_F64 ? 8 : ((mode == OM_F32 || mode == OM_F32_X64) ? 4 : 2); }
 inline int owner_acc_bytes(int mode) { return mode == OM_F64 ? 8 : 4; }   // window x, sums, spill
 inline int owner_vec_bytes(int mode) { return (mode == OM_F64 || mode >= OM_F32_X64) ? 8 : 4; }  // x, y
+__host__ __device__ constexpr int owner_block(int mode, int rk) {
+  return (mode == OM_BF16 || mode == OM_BF16_X64) && rk == 1 ? 8 : 4;
+}
+constexpr int kOwnerMaxBlock = 8;
 
 // Kernel shape: threads per CTA and CTAs per SM the window budget is sized for.
 // Four CTAs of 256 threads per SM for every column count: wider passes get smaller bands (a

@@ -131,14 +131,23 @@ __device__ __forceinline__ void owner_fma_batch(const A* xs, int m0, int len, co
   }
 }
 
-// Block loads: the kOwnerBlock (= 4) consecutive slots / values of one lane's block, with
-// vector loads (the block starts on a multiple of 4 entries).
+// Block loads: the 4 or 8 consecutive slots / values of one lane's block, with vector loads
+// (the block starts on a multiple of its length in entries).
 __device__ __forceinline__ void owner_ld_block(const uint16_t* p, uint32_t (&s)[4]) {
   const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
   s[0] = w.x & 0xffffu;
   s[1] = w.x >> 16;
   s[2] = w.y & 0xffffu;
   s[3] = w.y >> 16;
+}
+__device__ __forceinline__ void owner_ld_block(const uint16_t* p, uint32_t (&s)[8]) {
+  const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+  const unsigned q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    s[2 * i] = q[i] & 0xffffu;
+    s[2 * i + 1] = q[i] >> 16;
+  }
 }
 __device__ __forceinline__ void owner_ldv_block(const double* p, double (&v)[4]) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(p));
@@ -162,15 +171,22 @@ __device__ __forceinline__ void owner_ldv_block(const uint16_t* p, uint16_t (&v)
   v[2] = (uint16_t)(w.y & 0xffffu);
   v[3] = (uint16_t)(w.y >> 16);
 }
+__device__ __forceinline__ void owner_ldv_block(const uint16_t* p, uint16_t (&v)[8]) {
+  const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+  const unsigned q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = (uint16_t)(q[i] & 0xffffu);
+    v[2 * i + 1] = (uint16_t)(q[i] >> 16);
+  }
+}
 
-// Loads of block bi of a slice's regular part (every lane active): the lane's kOwnerBlock
-// steps lie side by side at pS / pV + 32 * kOwnerBlock * bi, pS and pV pointing at the lane's
-// first block.
+// Loads of block bi of a slice's regular part (every lane active): the lane's U steps lie
+// side by side at pS / pV + 32 * U * bi, pS and pV pointing at the lane's first block.
 template <typename V, int U>
 __device__ __forceinline__ void owner_load_full(const uint16_t* __restrict__ pS, const V* __restrict__ pV, int bi,
                                                 uint32_t (&sv)[U], V (&vv)[U]) {
-  static_assert(U == kOwnerBlock, "a batch is one block");
-  const size_t o = (size_t)kOwnerLanes * kOwnerBlock * bi;
+  const size_t o = (size_t)kOwnerLanes * U * bi;
   owner_ld_block(pS + o, sv);
   owner_ldv_block(pV + o, vv);
 }
@@ -198,11 +214,35 @@ __device__ __forceinline__ void owner_fma_full(const A* xs, const uint32_t (&sv)
   }
 }
 
-// Steps per batch of loads: one block (two batches are in flight per warp).
-template <int ST>
-constexpr int owner_unroll(int) {
-  return kOwnerBlock;
+// The multiply-adds of a packed block of 8 steps with 2-byte (BF16) values: slot and value of
+// step 2i + h are the low (h = 0) or high (h = 1) half of word i of s and v.
+template <typename A, int RK>
+__device__ __forceinline__ void owner_fma_packed(const A* xs, const uint4& s, const uint4& v, A (&acc)[RK]) {
+  const unsigned sw[4] = {s.x, s.y, s.z, s.w};
+  const unsigned vw[4] = {v.x, v.y, v.z, v.w};
+  if constexpr (RK == 1) {
+    A xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = xs[(sw[u >> 1] >> (16 * (u & 1))) & 0xffffu];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const A a = __uint_as_float((u & 1) ? (vw[u >> 1] & 0xffff0000u) : (vw[u >> 1] << 16));
+      acc[0] = owner_fma(a, xv[u], acc[0]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      A xv[RK];
+      owner_window_x<A, RK>(xs, (sw[u >> 1] >> (16 * (u & 1))) & 0xffffu, xv);
+      const A a = __uint_as_float((u & 1) ? (vw[u >> 1] & 0xffff0000u) : (vw[u >> 1] << 16));
+#pragma unroll
+      for (int c = 0; c < RK; ++c) acc[c] = owner_fma(a, xv[c], acc[c]);
+    }
+  }
 }
+
+// Steps of a ragged-tail batch (the regular part's batches are blocks of owner_block(ST, RK)).
+constexpr int kOwnerRaggedBatch = 4;
 
 // Band b of the product described by a, run by the whole CTA.
 template <int ST, int RK>
@@ -210,7 +250,8 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
   using V = typename OwnerTypes<ST>::V;
   using X = typename OwnerTypes<ST>::X;
   using A = typename OwnerTypes<ST>::A;
-  constexpr int U = owner_unroll<ST>(RK);
+  constexpr int U = owner_block(ST, RK);  // steps per block of the regular part
+  constexpr int R = kOwnerRaggedBatch;
   extern __shared__ __align__(16) unsigned char owner_smem[];
   A* xs = reinterpret_cast<A*>(owner_smem);  // window: x of slot s, column c at s * RK + c
   const int4 bd = __ldg(a.band + b);
@@ -280,15 +321,42 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
     A acc[RK];
 #pragma unroll
     for (int c = 0; c < RK; ++c) acc[c] = A(0);
-    // Regular part: the steps of whole blocks below minlen hold all 32 lanes, each lane's steps
-    // of a block side by side (internal.h), so each lane reads a block with vector loads. Two
-    // batches (blocks) of U steps are in flight
-    // in a ring of registers: a batch's loads are issued two compute phases before its
-    // multiply-adds, so that memory latency overlaps this and other warps' arithmetic.
-    const uint16_t* __restrict__ pS = S + base + kOwnerBlock * lane;
-    const V* __restrict__ pV = Vv + base + kOwnerBlock * lane;
+    // Regular part: the steps of whole blocks below minlen hold all 32 lanes, each lane's U
+    // steps of a block side by side, so each lane reads a block with vector loads. Two blocks
+    // are in flight in a ring of registers: a block's loads are issued two compute phases before
+    // its multiply-adds, so that memory latency overlaps this and other warps' arithmetic.
+    const uint16_t* __restrict__ pS = S + base + U * lane;
+    const V* __restrict__ pV = Vv + base + U * lane;
     const int nfull = minlen / U;  // batches of U steps with every lane active
-    {
+    if constexpr (sizeof(V) == 2 && U == 8) {
+      // 2-byte values: a block is one 16-byte word of slots and one of values, kept packed in
+      // the ring (8 registers per block) and unpacked at the multiply-adds
+      uint4 s0 = make_uint4(0, 0, 0, 0), s1 = s0, v0 = s0, v1 = s0;
+      const uint4* __restrict__ qS = reinterpret_cast<const uint4*>(pS);
+      const uint4* __restrict__ qV = reinterpret_cast<const uint4*>(pV);
+      if (nfull > 0) {
+        s0 = __ldg(qS);
+        v0 = __ldg(qV);
+      }
+      if (nfull > 1) {
+        s1 = __ldg(qS + kOwnerLanes);
+        v1 = __ldg(qV + kOwnerLanes);
+      }
+      int bi = 0;
+      for (; bi + 1 < nfull; bi += 2) {
+        owner_fma_packed<A, RK>(xs, s0, v0, acc);
+        if (bi + 2 < nfull) {
+          s0 = __ldg(qS + (size_t)kOwnerLanes * (bi + 2));
+          v0 = __ldg(qV + (size_t)kOwnerLanes * (bi + 2));
+        }
+        owner_fma_packed<A, RK>(xs, s1, v1, acc);
+        if (bi + 3 < nfull) {
+          s1 = __ldg(qS + (size_t)kOwnerLanes * (bi + 3));
+          v1 = __ldg(qV + (size_t)kOwnerLanes * (bi + 3));
+        }
+      }
+      if (bi < nfull) owner_fma_packed<A, RK>(xs, s0, v0, acc);
+    } else {
       uint32_t s0[U], s1[U];
       V v0[U], v1[U];
       if (nfull > 0) owner_load_full<V, U>(pS, pV, 0, s0, v0);
@@ -305,11 +373,11 @@ __device__ __forceinline__ void owner_body(const OwnerArgs& a, const int b) {
     // Ragged tail: steps m >= nfull * U, where lanes whose list has ended drop out; step m
     // holds one entry for each lane whose list is longer than m (those lanes come first).
     int64_t off = base + (int64_t)kOwnerLanes * nfull * U;
-    for (int m0 = nfull * U; m0 < maxlen; m0 += U) {
-      uint32_t sv[U];
-      V vv[U];
-      owner_load_batch<V, U>(S, Vv, m0, len, lane, off, sv, vv);
-      owner_fma_batch<A, V, U, RK>(xs, m0, len, sv, vv, acc);
+    for (int m0 = nfull * U; m0 < maxlen; m0 += R) {
+      uint32_t sv[R];
+      V vv[R];
+      owner_load_batch<V, R>(S, Vv, m0, len, lane, off, sv, vv);
+      owner_fma_batch<A, V, R, RK>(xs, m0, len, sv, vv, acc);
     }
     if (slot < nsp) {
       A* sp = static_cast<A*>(a.spill) + (size_t)spos * a.lds;

@@ -91,8 +91,8 @@ struct Layout {
 // Second pass: the lists of band b, written in its region [e0, e_end) of the entry arrays.
 // Returns false when a list is longer than kOwnerMaxLength.
 bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, const PlanBand& pb, const int4& bd,
-               int32_t q0, int64_t e0, int64_t e_end, Scratch& sc, int64_t* slice_off, uint32_t* lane, uint16_t* S,
-               int64_t* code, int32_t* spill_row, int64_t* lane_steps) {
+               int32_t q0, int64_t e0, int64_t e_end, int blk, Scratch& sc, int64_t* slice_off, uint32_t* lane,
+               uint16_t* S, int64_t* code, int32_t* spill_row, int64_t* lane_steps) {
   const int32_t r0 = pb.r0, r1 = pb.r1;
   collect_spill_rows(ia, ja, r0, r1, sc);
   const int32_t nsp = (int32_t)sc.sp.size();
@@ -143,14 +143,14 @@ bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, c
         lw[l] = kOwnerPadSlot;  // length 0
       }
     }
-    E = (E + kOwnerBlock - 1) / kOwnerBlock * kOwnerBlock;  // slices start on a block boundary
+    E = (E + blk - 1) / blk * blk;  // slices start on a block boundary
     slice_off[(size_t)q0 + q] = E;
     const int64_t base = E;
     const int32_t maxlen = sc.len[(size_t)sc.order[(size_t)a]];
     // regular part: the steps below the shortest list (lane 31's; 0 when lanes are unused), in
-    // whole blocks of kOwnerBlock steps, each lane's steps of a block side by side
+    // whole blocks of blk steps, each lane's steps of a block side by side
     const int32_t minlen = cnt == kOwnerLanes ? sc.len[(size_t)sc.order[(size_t)a + cnt - 1]] : 0;
-    const int32_t regular = minlen / kOwnerBlock * kOwnerBlock;
+    const int32_t regular = minlen / blk * blk;
     *lane_steps += (int64_t)kOwnerLanes * maxlen;
     int32_t active = cnt;  // lanes whose list is longer than m (a prefix: lengths descend)
     for (int32_t m = 0; m < maxlen; ++m) {
@@ -182,8 +182,7 @@ bool fill_band(const std::vector<int32_t>& ia, const std::vector<int32_t>& ja, c
           c = ((int64_t)(k0 + sc.upk[(size_t)qq]) << 2) | 2;  // scattered pair: au[k] with x of its row
           s = nsp + (sc.upr[(size_t)qq] - r0);
         }
-        const int64_t pos = m < regular ? base + (int64_t)kOwnerLanes * kOwnerBlock * (m / kOwnerBlock) +
-                                              (int64_t)kOwnerBlock * l + m % kOwnerBlock
+        const int64_t pos = m < regular ? base + (int64_t)kOwnerLanes * blk * (m / blk) + (int64_t)blk * l + m % blk
                                         : E + l;
         S[(size_t)pos] = (uint16_t)s;
         code[(size_t)pos] = c;
@@ -232,6 +231,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
                              const void* al, const void* au, const void* ad, bool sym, OwnerPlan& out) {
   (void)h;
   const int slot_bytes = owner_acc_bytes(mode), spill_bytes = owner_acc_bytes(mode);
+  const int blk = owner_block(mode, rk);
   const int vbytes = owner_value_bytes(mode);
   free_owner_plan(out);
   const int workers = std::max(1, std::min<int>(worker_count(), n / 4096 + 1));
@@ -273,8 +273,8 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
     L.band_slice[(size_t)b + 1] = L.band_slice[(size_t)b] + (nslots + kOwnerLanes - 1) / kOwnerLanes;
     // the band's region: its entries plus room to start every slice on a block boundary
     const int64_t need = nown + 2 * ((int64_t)ia[(size_t)pb.r1] - ia[(size_t)pb.r0]) +
-                         (int64_t)(kOwnerBlock - 1) * ((nslots + kOwnerLanes - 1) / kOwnerLanes);
-    L.band_entry[(size_t)b + 1] = L.band_entry[(size_t)b] + (need + kOwnerBlock - 1) / kOwnerBlock * kOwnerBlock;
+                         (int64_t)(blk - 1) * ((nslots + kOwnerLanes - 1) / kOwnerLanes);
+    L.band_entry[(size_t)b + 1] = L.band_entry[(size_t)b] + (need + blk - 1) / blk * blk;
     entries_used += nown + 2 * ((int64_t)ia[(size_t)pb.r1] - ia[(size_t)pb.r0]);
   }
   const int64_t nslices = L.band_slice[(size_t)nb];
@@ -294,7 +294,7 @@ csrc_status build_owner_plan(int32_t n, int64_t h, const std::vector<int32_t>& i
       const int32_t b = next.fetch_add(1);
       if (b >= nb) break;
       if (!fill_band(ia, ja, bands[(size_t)b], L.band[(size_t)b], L.band_slice[(size_t)b],
-                     L.band_entry[(size_t)b], L.band_entry[(size_t)b + 1], sc, slice_off.data(), lane.data(),
+                     L.band_entry[(size_t)b], L.band_entry[(size_t)b + 1], blk, sc, slice_off.data(), lane.data(),
                      S.data(), code.data(), spill_row.data(), &steps[(size_t)w]))
         fits = false;
     }
