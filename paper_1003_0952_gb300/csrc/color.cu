@@ -254,9 +254,15 @@ __global__ void __launch_bounds__(kColorThreads, 4) color_persistent_kernel(Colo
   // the group's first row of class c and its first chunk, loaded ahead
   int4 nd = make_int4(-1, 0, 0, 0);
   ColorChunk<V> nch;
+  // the group's second and third rows of the class: their descriptors too (q1v_96 with the JP
+  // colouring: 1.33 -> 1.23 ms)
+  int4 nd2 = make_int4(-1, 0, 0, 0), nd3 = make_int4(-1, 0, 0, 0);
   auto load_first = [&](int c) {
     const int idx = __ldg(a.color_ptr + c) + gid;
-    nd = idx < __ldg(a.color_ptr + c + 1) ? __ldg(a.desc + idx) : make_int4(-1, 0, 0, 0);
+    const int pe = __ldg(a.color_ptr + c + 1);
+    nd = idx < pe ? __ldg(a.desc + idx) : make_int4(-1, 0, 0, 0);
+    nd2 = idx + ngroups < pe ? __ldg(a.desc + idx + ngroups) : make_int4(-1, 0, 0, 0);
+    nd3 = idx + 2 * ngroups < pe ? __ldg(a.desc + idx + 2 * ngroups) : make_int4(-1, 0, 0, 0);
     color_load_chunk<V>(a, nd.x >= 0 ? nd.y + kColorU * gl : 0, nd.x >= 0 ? nd.z : 0, nch);
   };
   load_first(0);
@@ -264,7 +270,8 @@ __global__ void __launch_bounds__(kColorThreads, 4) color_persistent_kernel(Colo
     const int p1 = __ldg(a.color_ptr + c + 1);
     if (nd.x >= 0) color_row<V, X, G>(a, nd, nch, gl, gmask);
     for (int idx = __ldg(a.color_ptr + c) + gid + ngroups; idx < p1; idx += ngroups) {
-      const int4 d = __ldg(a.desc + idx);
+      const int i0 = __ldg(a.color_ptr + c) + gid;
+      const int4 d = idx == i0 + ngroups ? nd2 : (idx == i0 + 2 * ngroups ? nd3 : __ldg(a.desc + idx));
       ColorChunk<V> ch;
       color_load_chunk<V>(a, d.y + kColorU * gl, d.z, ch);
       color_row<V, X, G>(a, d, ch, gl, gmask);
