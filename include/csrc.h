@@ -271,7 +271,8 @@ csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* 
  * creates its handle and calls csrc_partition once at set-up, then uses this call.
  *
  * It computes what csrc_spmv / csrc_spmv_t compute with CSRC_STRAT_WINDOW, with the
- * same kernels (bit for bit: the window strategy sums every row in a fixed order). The only difference is that the spilled partial sums go to a fixed
+ * same kernels (bit for bit: the window strategy sums every row in a fixed order). The
+ * only difference is that the spilled partial sums go to a fixed
  * array of CSRC_NOALLOC_MAX_SPILL_ENTRIES values that the library holds in static
  * device memory (16 MiB on every GPU that loads the library, kept until the process
  * exits), instead of the buffer the handle allocates.
