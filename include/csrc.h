@@ -236,7 +236,13 @@ csrc_status csrc_color(csrc_handle h, uint64_t seed, int32_t* ncolors_out, int32
  */
 csrc_status csrc_color_stride(csrc_handle h, int64_t stride, int32_t* ncolors_out, int32_t* colors_out);
 
-/* y = A x (Fig. 2(a)) with the given strategy. Asynchronous on stream. */
+/*
+ * y = A x (Fig. 2(a)) with the given strategy (CSRC_STRAT_AUTO: the handle's tuned strategy,
+ * else the window strategy). x and y are device pointers, or host pointers that the call
+ * stages through handle-owned device buffers. Asynchronous on stream, except that a call
+ * that finds no plan for its strategy (no csrc_partition yet, or plans dropped by a change of
+ * band count or precision) first builds one, synchronously and allocating.
+ */
 csrc_status csrc_spmv(csrc_handle h, const void* x, void* y, csrc_strategy strategy, cudaStream_t stream);
 
 /* y = A^T x: the same kernels with al and au swapped (Section 5). */
@@ -244,17 +250,23 @@ csrc_status csrc_spmv_t(csrc_handle h, const void* x, void* y, csrc_strategy str
 
 /*
  * Batched products Y_b = A_b X_b (or A_b^T X_b) for b < batch, each X_b, Y_b an
- * n_b-by-nrhs row-major device block (double for CSRC_F64 storage, else float).
- * All handles must share one storage type. With nrhs = 1, one persistent kernel per
- * lanes-per-row class walks a work list of (matrix, band) tiles over all members, largest
- * bands first, and a second kernel folds every member's spilled partial sums; the launches
- * are captured in a CUDA graph and replayed while the arguments stay the same. Each member
- * runs a plan of its own for batches (bands of about 160,000 non-zeros, since the other
- * members fill the GPU) with the window strategy, or the atomic strategy when its windows
- * cannot hold every target. With nrhs > 1 the members run one after another through the
- * several-right-hand-side path.
- * Asynchronous on stream.
- * Errors: INVALID_ARG, MISMATCH, ALIAS, OUT_OF_MEMORY, CUDA.
+ * n_b-by-nrhs row-major device block: double for a CSRC_F64 handle (whatever its
+ * csrc_set_precision), float for CSRC_F32 / CSRC_BF16 storage. Members may differ in
+ * storage type and precision; all must live on the current device and be square.
+ * One vector of one matrix (batch = 1, nrhs = 1) is csrc_spmv / csrc_spmv_t with the
+ * handle's tuned strategy. Otherwise every member's columns are cut into chunks of 1, 2, 4
+ * or 8 (csrc_autotune_spmm picks the width) and every chunk's bands become tiles of one
+ * window-strategy launch per (value type, chunk width), costliest tiles first, followed by
+ * one accumulation launch per value type; the launches are captured in a CUDA graph and
+ * replayed while the handles, pointers and sizes stay the same. Each member runs plans of
+ * its own for batches (bands of up to about 100,000 non-zeros in FP64 and 180,000 in FP32 /
+ * BF16, smaller when the whole batch would not fill the GPU several times over). With
+ * nrhs = 1, a member tuned to another strategy, or whose windows cannot hold its targets,
+ * runs its own launches on the same stream after the graph.
+ * Asynchronous on stream; the first call with a new set of arguments builds plans and the
+ * graph (synchronous, allocating).
+ * Errors: INVALID_ARG (null or host pointers, rectangular handles, handles of another
+ * device), ALIAS, OUT_OF_MEMORY, CUDA.
  */
 csrc_status csrc_spmm_batched(const csrc_handle* hs, int32_t batch, const void* const* X, void* const* Y,
                               int32_t nrhs, int32_t transpose, cudaStream_t stream);
