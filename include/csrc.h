@@ -199,10 +199,12 @@ csrc_status csrc_create_from_coo(csrc_handle* out, int32_t n, int64_t nnz, const
  * Non-zero-guided row partition (Section 3.1): nbands contiguous row bands. Row i
  * weighs w_i = 1 + 2*(ia[i+1]-ia[i]) (the w_i sum to nnz). Boundary b_t is the
  * smallest r whose prefix weight P(r) satisfies P(r)*nbands >= t*nnz, so b_0 = 0
- * and b_nbands = n. nbands = 0 picks a count from the matrix and the GPU
- * (a multiple of the SM count). The window plan that the band kernels run is
- * built from these bands, and a band whose window would not fit in shared memory
- * is split further. Both are cached in the handle. Synchronous.
+ * and b_nbands = n. nbands = 0 picks a count from the matrix and the GPU: whole
+ * waves of SMs x 4 bands, each of about 100,000 non-zeros for FP64 values and 180,000
+ * for FP32 / BF16. The window plan that the kernels run is built from these bands; a
+ * band whose window would not fit in shared memory is split in two, and an automatic
+ * count that needed splits is replaced by the next whole number of waves, so that
+ * the bands stay equal. Both are cached in the handle. Synchronous.
  *   band_ptr_out  host int32[nbands+1] (nullable). Receives b_0..b_nbands.
  *                 With nbands = 0 it must hold csrc_info.nbands+1 entries.
  * Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA.
@@ -311,10 +313,12 @@ csrc_status csrc_spmv_noalloc(csrc_handle h, const void* x, void* y, int32_t tra
 /*
  * Autotuner (not in the paper, whose comparison of colouring and local buffers in
  * Section 4.2 shows that the best strategy depends on the matrix). Times y = A x with
- * every applicable strategy (window, atomic, and colour when csrc_color has run) and
- * several band counts (automatic, one and four per SM), then keeps the fastest band
- * count as the handle's partition and the fastest strategy as its CSRC_STRAT_AUTO
- * choice; batched products use it per member. Synchronous on stream.
+ * the window strategy at three band counts (the automatic one, one wave of SMs x 4 bands
+ * fewer and one more), then with the window-atomic and atomic strategies and, when the
+ * rows are coloured, the colour strategy. Keeps the fastest band count for the window
+ * plans and the fastest strategy as the handle's CSRC_STRAT_AUTO choice, and records
+ * both in the tuning cache (csrc_tune_key). Batched products keep a member's choice for
+ * single vectors. Synchronous on stream.
  *   x, y  device vectors of n elements used as scratch (y is overwritten)
  * Errors: INVALID_ARG (null or host pointers), OUT_OF_MEMORY, CUDA.
  */
