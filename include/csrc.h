@@ -325,9 +325,10 @@ csrc_status csrc_spmv_noalloc(csrc_handle h, const void* x, void* y, int32_t tra
 csrc_status csrc_autotune(csrc_handle h, const void* x, void* y, cudaStream_t stream);
 
 /*
- * Pick the columns per pass (2, 4 or 8) of several-right-hand-side products on this
- * handle by timing Y = A X on the caller's n-by-nrhs row-major device blocks X and Y
- * (Y is overwritten). Synchronous on stream. nrhs = 1 leaves the handle unchanged.
+ * Pick the columns per pass (1, 2, 4 or 8, at most nrhs) of several-right-hand-side
+ * products on this handle by timing Y = A X on the caller's n-by-nrhs row-major device
+ * blocks X and Y (Y is overwritten); the choice is recorded in the tuning cache for this
+ * nrhs. Synchronous on stream. nrhs = 1 leaves the handle unchanged.
  * Errors: INVALID_ARG, NOT_PARTITIONED, OUT_OF_MEMORY, CUDA.
  */
 csrc_status csrc_autotune_spmm(csrc_handle h, const void* X, void* Y, int32_t nrhs, cudaStream_t stream);
